@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the FermiNet VMC step on GB300.
+
+One step = the whole hot path over one batch of walkers: the workload's
+Metropolis moves (value passes), log|psi| and the local energy (tangent pass),
+and the VMC energy gradient (adjoint) -- all through the C ABI of libferminet.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VMC walker-steps/sec (psi, E_L, grad) vs plain FP32 path at stated error"
+UNIT = "walker-steps/s"
+DEFAULT_WORKLOAD = "c4h6"
+L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
+
+
+def describe(wl) -> str:
+    t = wl.net
+    geo = f"{len(wl.geoms)} geometries" if len(wl.geoms) > 1 else f"{t.n_nuc} nuclei"
+    return (f"{wl.name}: {geo}, {t.n_elec} electrons ({t.n_up}/{t.n_down}), L={t.n_layers}, d1={t.d1}, "
+            f"d2={t.d2}, K={t.n_det} determinants, {wl.batch} walkers; step = {wl.mcmc_steps} Metropolis moves "
+            f"(width {wl.mcmc_width}) + log|psi| + E_L + VMC energy gradient")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _num(d, *keys):
+    for k in keys:
+        v = d.get(k)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("value", "gbs", "tflops"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step_sample(wl, P, x, counter):
+    """One step of the oracle on walkers x (a bounded sample, all on the first
+    geometry): Metropolis moves, local energy and VMC gradient.
+    Returns (seconds, E_L, positions after the moves)."""
+    import oracle
+    from paper_2011_07125_gb300 import synth
+    geoms = wl.geoms[:1]
+    t0 = time.perf_counter()
+    lp, _ = oracle.logpsi(wl.net, P, geoms, x)
+    x2, lp2, _, _ = oracle.mcmc(wl.net, P, geoms, x, lp, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, counter)
+    out = oracle.local_energy(wl.net, P, geoms, x2)
+    oracle.energy_grad(wl.net, P, geoms, x2, out["eloc"])
+    return time.perf_counter() - t0, out["eloc"], x2
+
+
+def cpu_sample_size(wl, P, x, target_s: float) -> int:
+    """Walkers per oracle sample so that one sample takes about target_s on
+    all host cores (calibrated on one walker)."""
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t1, _, _ = oracle_step_sample(wl, P, x[:1], 0)
+    n = int(cores * target_s / max(t1, 1e-3))
+    n = max(1, min(n, wl.batch, 64 * cores))
+    return n
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 oracle as it stands, on the host cores."""
+    import numpy as np
+    import oracle
+    from paper_2011_07125_gb300 import synth
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    lay = oracle.layout(wl.net)
+    P = synth.init_params(lay)
+    xall = synth.init_walkers(wl)
+    per_step_s = max(2.0, 150.0 / max(args.steps + args.warmup, 1))
+    S = cpu_sample_size(wl, P, xall, per_step_s)
+    times = []
+    for k in range(args.warmup + args.steps):
+        xs = xall[(k * S) % max(wl.batch - S, 1):][:S] if wl.batch > S else xall
+        dt, _, _ = oracle_step_sample(wl, P, xs, k * wl.mcmc_steps)
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = S * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times) * wl.batch / S,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded walkers, N(0,1/fan_in) weights)",
+            "config": {"workload": describe(wl), "walkers": wl.batch, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{S} walkers per step of the {wl.batch}-walker batch; ms_per_step scaled "
+                                       f"to the full batch"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def tangent_roofline(fn, prec, clocks, pk, pk_kind):
+    r = fn.profile_read("tangent_gemm")
+    if r["launches"] == 0 or r["ms"] <= 0:
+        return None
+    achieved = r["alg_flops"] / (r["ms"] * 1e-3) / 1e12
+    if prec == "fp32":
+        mhz = clocks.get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        bound, note = "alu", f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz"
+    else:
+        peak = _num(pk, "bf16_tflops_sustained", "bf16_tflops") or 1700.0
+        bound, note = "tensor", f"bf16 sustained, {pk_kind}"
+    return {"bound": bound, "kernel": "layer + orbital GEMMs of the local-energy pass", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "launches": r["launches"], "avg_launch_ms": r["ms"] / r["launches"], "peak_note": note}
+
+
+def run_gpu(args, wl):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2011_07125_gb300 import synth
+    from paper_2011_07125_gb300.binding import FermiNet, launch_count
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    prec = args.precision or "fp32"
+    fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision=prec)
+    P = synth.init_params(fn.layout)
+    x0 = synth.init_walkers(wl, synth.SEED_WALKERS + rank)
+    params = torch.from_numpy(P).to(dev)
+    fn.set_params(params)
+    x = torch.from_numpy(x0).to(dev)
+    lp = fn.logpsi(x, with_sign=False)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    counter = [0]
+
+    def step():
+        fn.mcmc_step(x, lp, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, counter[0])
+        counter[0] += wl.mcmc_steps
+        out = fn.local_energy(x)
+        em, g = fn.energy_grad(x, out["eloc"])
+        return out, em, g
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fn.profile(True)
+    l0 = launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # L2 flush outside the timed events
+            evs[k][0].record(s)
+            out, em, g = step()
+            evs[k][1].record(s)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = launch_count() - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = cs.summary()
+    st = fn.sync()
+    pk, pk_kind = peaks()
+    roof = tangent_roofline(fn, prec, clocks, pk, pk_kind)
+    classes = {k: fn.profile_read(k) for k in ("tangent_gemm", "det_tangent", "two_layer", "means", "tanh",
+                                                 "value_pass", "adjoint")}
+    fn.profile(False)
+    ms_per_step = ms / args.steps
+    value = world * wl.batch * args.steps / (ms * 1e-3)
+
+    # plain FP32 path on the same workload (the metric's comparison), when the timed path is mixed
+    fp32 = None
+    if prec != "fp32" and not args.no_fp32_compare:
+        f32 = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision="fp32")
+        f32.set_params(params)
+        xs = torch.from_numpy(x0).to(dev)
+        lps = f32.logpsi(xs, with_sign=False)
+        c2 = [0]
+
+        def step32():
+            f32.mcmc_step(xs, lps, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, c2[0])
+            c2[0] += wl.mcmc_steps
+            o = f32.local_energy(xs)
+            f32.energy_grad(xs, o["eloc"])
+
+        for _ in range(max(1, args.warmup // 2)):
+            step32()
+        torch.cuda.synchronize()
+        t32 = 0.0
+        for k in range(max(2, args.steps // 2)):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            step32()
+            b.record(s)
+            torch.cuda.synchronize()
+            t32 += a.elapsed_time(b)
+        n32 = max(2, args.steps // 2)
+        fp32 = {"value": wl.batch * n32 / (t32 * 1e-3), "unit": UNIT, "ms_per_step": t32 / n32}
+        f32.close()
+
+    # end to end through the public API: host (pinned) walkers in, energy and gradient out, every step
+    xh = torch.from_numpy(x0).pin_memory()
+    eh = torch.empty(wl.batch, dtype=torch.float32).pin_memory()
+    gh = torch.empty(fn.n_params, dtype=torch.float32).pin_memory()
+    mh = torch.empty(len(wl.geoms), dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(x)
+    n_e2e = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    for k in range(n_e2e):
+        xd.copy_(xh, non_blocking=True)
+        lpd = fn.logpsi(xd, with_sign=False)
+        fn.mcmc_step(xd, lpd, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, 10 ** 6 + k * wl.mcmc_steps)
+        o = fn.local_energy(xd)
+        em2, g2 = fn.energy_grad(xd, o["eloc"])
+        xh.copy_(xd, non_blocking=True)
+        eh.copy_(o["eloc"], non_blocking=True)
+        gh.copy_(g2, non_blocking=True)
+        mh.copy_(em2, non_blocking=True)
+    t1.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / n_e2e
+    e2e = {"value": world * wl.batch / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(xh.numel() * 4),
+           "d2h_bytes_per_step": int(xh.numel() * 4 + eh.numel() * 4 + gh.numel() * 4 + mh.numel() * 8),
+           "note": "includes one extra log|psi| pass per step for the uploaded walkers"}
+
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        import oracle
+        xs_np = x.cpu().numpy().astype(np.float32)
+        S = cpu_sample_size(wl, P, xs_np, 15.0)
+        xs_np = xs_np[:S]
+        dt, eloc_o, _ = oracle_step_sample(wl, P, xs_np, 0)
+        cpu = {"value": S / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+               "sample": f"{S} walkers of the {wl.batch}-walker batch ({wl.mcmc_steps} moves + E_L + gradient), "
+                         f"{dt:.1f} s"}
+        # error of the timed path on the same sampled walkers (current positions)
+        o = fn.local_energy(x[:S].contiguous()) if len(wl.geoms) == 1 else None
+        if o is not None:
+            ref = oracle.local_energy(wl.net, P, wl.geoms[:1], xs_np)
+            de = np.abs(o["eloc"].cpu().numpy() - ref["eloc"])
+            err = {"walkers": S, "eloc_max_abs": float(de.max()), "eloc_median_abs": float(np.median(de)),
+                   "eloc_mean_err": float(abs(o["eloc"].cpu().numpy().mean() - ref["eloc"].mean())),
+                   "logpsi_max_rel": float((np.abs(o["logpsi"].cpu().numpy() - ref["logpsi"]) /
+                                            np.maximum(np.abs(ref["logpsi"]), 1)).max())}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16/f32",
+                "data": "synthetic (seeded walkers, N(0,1/fan_in) weights; the paper ships no data)",
+                "config": {"workload": describe(wl), "walkers": wl.batch, "precision": prec,
+                           "l2": "256 MiB buffer written between timed steps, outside the timed events",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "status": st, "fp32_path": fp32, "error_vs_oracle": err,
+                "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in classes.items()}}
+        print(json.dumps(line), flush=True)
+    fn.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default=None, choices=[None, "fp32", "mixed"])
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from paper_2011_07125_gb300 import synth
+    wl = synth.workload(args.workload)
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, wl)
+        return
+    run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * ferminet.h — C ABI of the GB300 (sm_103a) FermiNet VMC hot path.
+ *
+ * Method: "Better, Faster Fermionic Neural Networks" (Spencer, Pfau, Botev,
+ * Foulkes, arXiv:2011.07125).  Over a batch of MCMC walkers the library
+ * evaluates
+ *   - log|psi| and sign of the multi-determinant Ansatz of Eq. 3 (determinant
+ *     weights omega_k removed, Sec. 3) built from the isotropic-envelope
+ *     orbitals of Eq. 4 (scalar sigma per orbital and nucleus, Sec. 3);
+ *   - the local energy psi^-1 H psi of the Born-Oppenheimer Hamiltonian of
+ *     Eq. 1: kinetic -1/2 (lap log|psi| + |grad log|psi||^2) over all 3n
+ *     electron coordinates (forward-mode derivatives, Sec. 3) plus the
+ *     electron-electron, electron-nucleus and nucleus-nucleus Coulomb sums;
+ *   - the gradient of the VMC energy of Eq. 2 with respect to the parameters,
+ *     2/B sum_w (E_L,w - E_mean) d log|psi_w| / d theta, through a hand-written
+ *     adjoint;
+ *   - Gaussian all-electron Metropolis moves sampling |psi|^2 (Eq. 2).
+ *
+ * Conventions (all entry points):
+ *   - Every pointer argument named d_* is a DEVICE pointer owned by the caller;
+ *     the library never frees it and keeps no reference after the call returns.
+ *     Host pointers (geometry arrays, the layout table) are read during the call.
+ *   - Electron coordinates are float32, row-major [walker][electron][xyz],
+ *     up-spin electrons first.  Units are bohr and hartree.
+ *   - All device work is enqueued asynchronously on the stream given to
+ *     ferminet_init; results are valid once that stream has been synchronised.
+ *   - Argument errors are reported synchronously through the return status
+ *     (FN_EINVAL) and ferminet_last_error(); no exception crosses the ABI.
+ *   - Device-side conditions (a singular orbital matrix, non-finite output) are
+ *     counted in a device status word read by ferminet_sync().
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef FERMINET_H
+#define FERMINET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FN_OK = 0,
+  FN_EINVAL = 1,     /* bad argument (shape, null pointer, batch size)          */
+  FN_ECUDA = 2,      /* a CUDA runtime call failed                             */
+  FN_ENOMEM = 3,     /* device workspace could not be allocated                */
+  FN_ENONFINITE = 4, /* ferminet_sync: some walker produced a non-finite value */
+  FN_ETIMEOUT = 5,   /* a bounded device wait expired                          */
+  FN_ESINGULAR = 6   /* ferminet_sync: some orbital matrix was singular        */
+} fn_status;
+
+typedef enum {
+  FN_PREC_FP32 = 0,  /* every contraction in FP32 on the CUDA cores            */
+  FN_PREC_MIXED = 1  /* tangent-pass layer GEMMs in BF16 on tcgen05 tensor
+                        cores with FP32 accumulation; orbitals, determinants
+                        and energies in FP32; reductions in FP64              */
+} fn_precision;
+
+/* Network shape.  L = n_layers one-electron layers (widths d1) and L-1
+ * two-electron layers (widths d2); K = n_det determinants; n_nuc nuclei per
+ * geometry (all geometries of a context share it). */
+typedef struct {
+  int n_layers, d1, d2, n_det, n_up, n_down, n_nuc;
+} fn_net;
+
+/* One nuclear geometry (host pointers): R [n_nuc][3] bohr, Z [n_nuc].
+ * Walkers [walker_offset, walker_offset + walker_count) of every batch belong
+ * to it.  With a single geometry the range is ignored (all walkers use it). */
+typedef struct {
+  const double* R;
+  const double* Z;
+  long walker_offset, walker_count;
+} fn_geometry;
+
+/* One block of the flat FP32 parameter vector.  kind: 0 = dense weight
+ * (conventionally initialised N(0, 1/fan_in)), 1 = bias (0), 2 = envelope
+ * weight pi or exponent sigma (1). */
+typedef struct {
+  char name[32];
+  long offset, count, fan_in;
+  int kind, pad;
+} fn_param_entry;
+
+typedef struct fn_ctx fn_ctx;
+
+/* Creates a context.  geoms: n_geoms >= 1 geometries; with n_geoms > 1 their
+ * walker ranges must tile [0, total) without overlap and every batch passed
+ * later must have B == total.  stream: a cudaStream_t (NULL = legacy default
+ * stream).  On success *out owns device memory until ferminet_destroy.
+ * Parameters start as all zeros; call ferminet_set_params. */
+fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms, fn_precision prec,
+                        void* stream, fn_ctx** out);
+
+/* Parameter layout (Eq. 3-4 plus the equivariant layers): fills up to
+ * max_entries entries of out (may be NULL), the entry count and the total
+ * parameter count.  Blocks, in order: for each layer l: V_l [d1][3 a + 2 e]
+ * (acting on [h_i, mean_up h, mean_down h, mean_up h_i., mean_down h_i.],
+ * a = 4 n_nuc or d1, e = 4 or d2), b_l [d1], and for l < L-1: W_l [d2][e],
+ * c_l [d2]; then w_orb_up [K][n_up][d1], w_orb_down [K][n_down][d1],
+ * g_orb_up [K][n_up], g_orb_down [K][n_down], pi_up / pi_down [K][n_s][n_nuc],
+ * sigma_up / sigma_down [K][n_s][n_nuc]. */
+fn_status ferminet_param_layout(const fn_ctx* ctx, fn_param_entry* out, int max_entries, int* n_entries,
+                                long* n_params);
+
+/* Same layout as ferminet_param_layout, computed from the shape alone (no
+ * context and no device needed).  Returns FN_EINVAL for an invalid shape. */
+fn_status ferminet_net_layout(const fn_net* net, fn_param_entry* out, int max_entries, int* n_entries,
+                              long* n_params);
+
+/* Copies n_params floats from d_params (device) into the library's parameter
+ * buffers (and refreshes the BF16 copies of the mixed path).  Stream-ordered. */
+fn_status ferminet_set_params(fn_ctx* ctx, const float* d_params);
+
+/* log|psi| and sign (Eq. 3) for B walkers.  d_x [B][n][3]; d_logpsi, d_sign [B]
+ * (d_sign may be NULL).  A walker whose psi is exactly zero gets -inf and 0. */
+fn_status ferminet_logpsi(fn_ctx* ctx, const float* d_x, long B, float* d_logpsi, float* d_sign);
+
+/* Local energy E_L = -1/2 (lap log|psi| + |grad log|psi||^2) + V (Eq. 1) for B
+ * walkers.  d_eloc [B] required; d_logpsi, d_sign, d_kinetic [B] optional
+ * (NULL to skip).  In FN_PREC_MIXED the tangent-pass layer GEMMs run in BF16. */
+fn_status ferminet_local_energy(fn_ctx* ctx, const float* d_x, long B, float* d_eloc, float* d_logpsi,
+                                float* d_sign, float* d_kinetic);
+
+/* Vector-Jacobian product of log|psi|: d_grad [n_params] (float) receives
+ * sum_w d_seeds[w] * d log|psi_w| / d theta.  d_seeds [B] float.  Used by the
+ * autograd binding (forward = log|psi|, backward = this call). */
+fn_status ferminet_logpsi_vjp(fn_ctx* ctx, const float* d_x, long B, const float* d_seeds, float* d_grad);
+
+/* VMC energy gradient (Eq. 2 differentiated with E_L held fixed).  For every
+ * geometry g, d_emean[g] (double, [n_geoms]) = mean of d_eloc over its walkers,
+ * and d_grad [n_params] = sum_g 2/B_g sum_{w in g} (E_L,w - E_mean,g)
+ * d log|psi_w| / d theta, reduced in FP64 and stored as float. */
+fn_status ferminet_energy_grad(fn_ctx* ctx, const float* d_x, long B, const float* d_eloc, double* d_emean,
+                               float* d_grad);
+
+/* n_steps Gaussian all-electron Metropolis moves sampling |psi|^2 (Eq. 2).
+ * Step s uses counter t = counter + s.  For walker w the proposal is
+ * x' = x + width * z with z drawn by Philox4x32-10 (key {seed lo, seed hi},
+ * counter {w, b, t lo, t hi} for normals 4b..4b+3 via Box-Muller, cos then
+ * sin, uniforms ((u32 >> 9) + 0.5) * 2^-23), and the move is accepted iff
+ * log u < 2 (log|psi(x')| - log|psi(x)|) with u from counter
+ * {w, 0xFFFFFFFF, t lo, t hi}, word 0.  d_x [B][n][3] and d_logpsi [B] are
+ * updated in place (d_logpsi must hold log|psi(d_x)| on entry);
+ * d_accepted [B] (int, may be NULL) receives the accepted-move count. */
+fn_status ferminet_mcmc_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_steps, float width,
+                             uint64_t seed, uint64_t counter, int* d_accepted);
+
+/* Synchronises the context stream and reads the device status word:
+ * FN_ESINGULAR / FN_ENONFINITE if any walker since the last sync had a
+ * singular orbital matrix or a non-finite output, else FN_OK or a CUDA error.
+ * Clears the status word. */
+fn_status ferminet_sync(fn_ctx* ctx);
+
+/* Number of orbital matrices whose FP32 pivot ratio min|u_kk| / max|u_kk| fell
+ * below the ill-conditioning threshold since the last call (reads a device
+ * counter; synchronises the stream). */
+long ferminet_flagged_matrices(fn_ctx* ctx);
+
+/* Kernel classes timed by ferminet_profile_read. */
+typedef enum {
+  FN_KC_TANGENT_GEMM = 0, /* layer and orbital GEMMs of the local-energy pass  */
+  FN_KC_DET_TANGENT = 1,  /* determinant + derivative-trace kernel (E_L pass)  */
+  FN_KC_TWO_LAYER = 2,    /* two-electron layer kernel (all passes)            */
+  FN_KC_MEANS = 3,        /* spin-mean kernels of the local-energy pass        */
+  FN_KC_TANH = 4,         /* forward-Laplacian tanh kernel                     */
+  FN_KC_VALUE_PASS = 5,   /* one whole value pass (log|psi| only)              */
+  FN_KC_ADJOINT = 6,      /* one whole adjoint (d log|psi| / d theta)          */
+  FN_KC_COUNT = 7
+} fn_kernel_class;
+
+/* Turns per-class timing on (enable != 0) or off and clears the totals.  While
+ * on, each launch of a timed class is bracketed by CUDA events recorded on the
+ * context stream. */
+fn_status ferminet_profile(fn_ctx* ctx, int enable);
+
+/* Synchronises the stream and returns, for one class since ferminet_profile:
+ * total event time (ms), number of timed launches, and the algorithmic
+ * floating-point operations of those launches (multiply-adds count 2; tangent
+ * columns counted without padding; orbital GEMMs counted for the same-spin
+ * block only).  Any output pointer may be NULL. */
+fn_status ferminet_profile_read(fn_ctx* ctx, int kernel_class, double* total_ms, long* launches,
+                                double* alg_flops);
+
+/* Kernels launched by this library in this process so far (all contexts). */
+long long ferminet_launch_count(void);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* ferminet_last_error(const fn_ctx* ctx);
+
+/* Releases all device memory of the context.  NULL is ignored. */
+void ferminet_destroy(fn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FERMINET_H */

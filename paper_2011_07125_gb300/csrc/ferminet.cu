@@ -1,0 +1,820 @@
+// C ABI of the FermiNet VMC hot path: context, parameter layout, workspace
+// planning and the per-call kernel schedules.
+//
+// Schedule of one network pass over a chunk of Bc walkers (value pass: one
+// column per activation row; tangent pass: C = tangent_cols(n) columns):
+//   features -> for each layer l:
+//       spin means of h^l (M1) and of h^l_ij (M2, expanded to dense columns)
+//       U  = M1 . [V_b V_c]^T            (per-walker part of the factored layer)
+//       Z  = h^l . V_a^T + M2 . [V_d V_e]^T + b + U
+//       h^{l+1} = tanh(Z) (+ h^l), forward-Laplacian rule on the columns
+//       h^{l+1}_ij = tanh(W h^l_ij + c) (+ h^l_ij)
+//   orbitals O = h^L . W_orb^T + g  -> determinants -> log|psi|, E_L.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "fn_internal.cuh"
+
+namespace fn {
+
+std::atomic<long long> g_launches{0};
+
+void build_layout(const fn_net& t, Layout* L) {
+  L->entries.clear();
+  long off = 0;
+  auto add = [&](long* field, const char* nm, long cnt, long fan, int kind) {
+    if (field) *field = off;
+    fn_param_entry e{};
+    snprintf(e.name, sizeof e.name, "%s", nm);
+    e.offset = off;
+    e.count = cnt;
+    e.fan_in = fan;
+    e.kind = kind;
+    L->entries.push_back(e);
+    off += cnt;
+  };
+  char nm[32];
+  for (int l = 0; l < t.n_layers; ++l) {
+    long a = din1_of(t, l), e = din2_of(t, l), fan = 3 * a + 2 * e;
+    snprintf(nm, sizeof nm, "V%d", l);
+    add(&L->V[l], nm, (long)t.d1 * fan, fan, 0);
+    snprintf(nm, sizeof nm, "b%d", l);
+    add(&L->b[l], nm, t.d1, 1, 1);
+    if (l < t.n_layers - 1) {
+      snprintf(nm, sizeof nm, "W%d", l);
+      add(&L->W[l], nm, (long)t.d2 * e, e, 0);
+      snprintf(nm, sizeof nm, "c%d", l);
+      add(&L->c[l], nm, t.d2, 1, 1);
+    }
+  }
+  const long K = t.n_det;
+  add(&L->w_orb, "w_orb_up", K * t.n_up * t.d1, t.d1, 0);
+  add(nullptr, "w_orb_down", K * t.n_down * t.d1, t.d1, 0);
+  add(&L->g_orb, "g_orb_up", K * t.n_up, 1, 1);
+  add(nullptr, "g_orb_down", K * t.n_down, 1, 1);
+  add(&L->pi[0], "pi_up", K * t.n_up * t.n_nuc, 1, 2);
+  add(&L->pi[1], "pi_down", K * t.n_down * t.n_nuc, 1, 2);
+  add(&L->sigma[0], "sigma_up", K * t.n_up * t.n_nuc, 1, 2);
+  add(&L->sigma[1], "sigma_down", K * t.n_down * t.n_nuc, 1, 2);
+  L->total = off;
+}
+
+}  // namespace fn
+
+using namespace fn;
+
+namespace {
+
+// Bump allocator over the context workspace.  In measuring mode it hands out
+// fake addresses and only records the total size.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  bool measure = true;
+  template <class T>
+  T* get(size_t n) {
+    size_t bytes = ((n * sizeof(T) + 255) / 256) * 256;
+    T* p = measure ? reinterpret_cast<T*>((uintptr_t)(4096 + off)) : reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+struct FwdOut {
+  float* logpsi = nullptr;
+  float* sign = nullptr;
+  float* eloc = nullptr;
+  float* kinetic = nullptr;
+};
+
+// Value-pass activations kept for the adjoint.
+struct Stored {
+  float* H[17] = {};
+  float* Y[16] = {};
+  float* E[17] = {};
+  float* Y2[16] = {};
+  float* M1[16] = {};
+  float* M2[16] = {};
+  float* O = nullptr;
+  float* minv = nullptr;
+  float* env = nullptr;
+  float* wdet = nullptr;
+};
+
+fn_status fail(fn_ctx* c, fn_status st, const char* msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+fn_status cuda_check(fn_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return FN_OK;
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return FN_ECUDA;
+}
+
+#define CK(call)                                                 \
+  do {                                                           \
+    fn_status _st = cuda_check(c, (call), #call);                \
+    if (_st != FN_OK) return _st;                                \
+  } while (0)
+
+cudaEvent_t take_event(fn_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets the launches issued during its lifetime with events on the context
+// stream when profiling is on.
+struct Prof {
+  fn_ctx* c;
+  int cls;
+  double flops;
+  cudaEvent_t e0 = nullptr;
+  Prof(fn_ctx* c_, int cls_, double fl) : c(c_), cls(cls_), flops(fl) {
+    if (c->prof_on && cls < FN_KC_COUNT) {
+      e0 = take_event(c);
+      cudaEventRecord(e0, c->stream);
+    }
+  }
+  ~Prof() {
+    if (e0) {
+      cudaEvent_t e1 = take_event(c);
+      cudaEventRecord(e1, c->stream);
+      c->pending.push_back({cls, e0, e1, flops});
+    }
+  }
+};
+
+void drain_profile(fn_ctx* c) {
+  if (c->pending.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.e0, p.e1);
+    c->prof_ms[p.cls] += ms;
+    c->prof_n[p.cls] += 1;
+    c->prof_flops[p.cls] += p.flops;
+    c->ev_pool.push_back(p.e0);
+    c->ev_pool.push_back(p.e1);
+  }
+  c->pending.clear();
+}
+
+Geo geo_of(fn_ctx* c) { return Geo{c->d_R, c->d_Z, c->d_Enn64, c->G > 1 ? c->d_geo : nullptr}; }
+
+// One network pass (see the file comment) over walkers [w0, w0 + Bc).
+void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangent, bool store, const FwdOut& out,
+             Stored* st) {
+  const fn_net& t = c->net;
+  const int n = c->n, N = c->N, L = t.n_layers, K = t.n_det, d1 = t.d1, d2 = t.d2;
+  const int C = tangent ? c->Ct : 1, Q = tangent ? kQ : 1;
+  const int Creal = tangent ? 3 * n + 2 : 1;
+  const long Ktot = (long)K * n;
+  const long rows = Bc * n * C;
+  const long pairs = Bc * n * n;
+  int max_din1 = std::max(4 * N, d1), max_din2 = std::max(4, d2);
+  float* H0 = ar.get<float>(rows * 4 * N);
+  float* E0 = ar.get<float>(pairs * Q * 4);
+  float *Ha = nullptr, *Hb = nullptr, *Ea = nullptr, *Eb = nullptr, *M1 = nullptr, *M2 = nullptr;
+  if (store) {
+    st->H[0] = H0;
+    st->E[0] = E0;
+    for (int l = 0; l < L; ++l) {
+      st->H[l + 1] = ar.get<float>(rows * d1);
+      st->Y[l] = ar.get<float>(Bc * n * d1);
+      st->M1[l] = ar.get<float>(Bc * C * 2 * din1_of(t, l));
+      st->M2[l] = ar.get<float>(rows * 2 * din2_of(t, l));
+      if (l < L - 1) {
+        st->E[l + 1] = ar.get<float>(pairs * Q * d2);
+        st->Y2[l] = ar.get<float>(pairs * d2);
+      }
+    }
+  } else {
+    Ha = ar.get<float>(rows * d1);
+    Hb = ar.get<float>(rows * d1);
+    if (L > 1) {
+      Ea = ar.get<float>(pairs * Q * d2);
+      Eb = ar.get<float>(pairs * Q * d2);
+    }
+    M1 = ar.get<float>(Bc * C * 2 * max_din1);
+    M2 = ar.get<float>(rows * 2 * max_din2);
+  }
+  float* U = ar.get<float>(Bc * C * d1);
+  float* Z = ar.get<float>(rows * d1);
+  float* O = ar.get<float>(rows * Ktot);
+  float* logdet = ar.get<float>(Bc * K * 2);
+  float* sgn = ar.get<float>(Bc * K * 2);
+  float* dgrad = tangent ? ar.get<float>(Bc * K * 2 * 3 * n) : nullptr;
+  float* dlap = tangent ? ar.get<float>(Bc * K * 2) : nullptr;
+  const long nss = (long)c->ns_max * c->ns_max;
+  if (store) {
+    st->O = O;
+    st->minv = ar.get<float>(Bc * K * 2 * nss);
+    st->env = ar.get<float>(Bc * K * 2 * nss);
+    st->wdet = ar.get<float>(Bc * K);
+  }
+  if (ar.measure) return;
+
+  cudaStream_t s = c->stream;
+  const float* P = c->d_params;
+  const Geo g = geo_of(c);
+  launch_features(s, x, Bc, w0, n, N, C, Q, g, H0, E0);
+  const float* Hc = H0;
+  const float* Ec = E0;
+  for (int l = 0; l < L; ++l) {
+    const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
+    const float* V = P + c->lay.V[l];
+    float* M1l = store ? st->M1[l] : M1;
+    float* M2l = store ? st->M2[l] : M2;
+    {
+      Prof pm(c, tangent ? FN_KC_MEANS : FN_KC_COUNT, 0.0);
+      launch_mean1(s, Hc, Bc, n, t.n_up, C, a1, M1l);
+      launch_mean2(s, Ec, Bc, n, t.n_up, Q, a2, C, M2l);
+    }
+    const double fl_rows = 2.0 * (double)Bc * Creal;  // algorithmic rows per walker-column, x2 for FMA
+    {
+      Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * d1 * 2.0 * a1);
+      gemm_nt(s, Bc * C, d1, 2 * a1, M1l, 2 * a1, V + a1, wV, U, d1, Epi{});
+    }
+    {
+      Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * n * d1 * (double)a1);
+      gemm_nt(s, rows, d1, a1, Hc, a1, V, wV, Z, d1, Epi{});
+    }
+    Epi e;
+    e.beta = 1.f;
+    e.bias = P + c->lay.b[l];
+    e.bias_period = C;
+    e.U = U;
+    e.u_div = (long)n * C;
+    e.u_mul = C;
+    e.u_mod = C;
+    e.ldu = d1;
+    {
+      Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * n * d1 * 2.0 * a2);
+      gemm_nt(s, rows, d1, 2 * a2, M2l, 2 * a2, V + 3 * a1, wV, Z, d1, e);
+    }
+    float* Hn = store ? st->H[l + 1] : ((l % 2 == 0) ? Ha : Hb);
+    {
+      Prof pt(c, tangent ? FN_KC_TANH : FN_KC_COUNT, 0.0);
+      launch_tanh_fl(s, Z, l >= 1 ? Hc : nullptr, Bc, n, C, d1, Hn, store ? st->Y[l] : nullptr);
+    }
+    if (l < L - 1) {
+      float* En = store ? st->E[l + 1] : ((l % 2 == 0) ? Ea : Eb);
+      Prof p2(c, FN_KC_TWO_LAYER, 2.0 * (double)pairs * (tangent ? kQ : 1) * d2 * a2);
+      launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En,
+                       store ? st->Y2[l] : nullptr);
+      Ec = En;
+    }
+    Hc = Hn;
+  }
+  Epi eo;
+  eo.bias = P + c->lay.g_orb;
+  eo.bias_period = C;
+  {
+    const double same_spin = (double)t.n_up * t.n_up + (double)t.n_down * t.n_down;
+    Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, 2.0 * (double)Bc * Creal * d1 * K * same_spin);
+    gemm_nt(s, rows, Ktot, d1, Hc, d1, P + c->lay.w_orb, d1, O, Ktot, eo);
+  }
+  DetArgs da{};
+  da.O = O;
+  da.ldo = Ktot;
+  da.C = C;
+  da.n = n;
+  da.n_up = t.n_up;
+  da.K = K;
+  da.N = N;
+  da.x = x;
+  da.g = g;
+  da.w0 = w0;
+  da.Bc = Bc;
+  da.pi[0] = P + c->lay.pi[0];
+  da.pi[1] = P + c->lay.pi[1];
+  da.sigma[0] = P + c->lay.sigma[0];
+  da.sigma[1] = P + c->lay.sigma[1];
+  da.tangent = tangent;
+  da.logdet = logdet;
+  da.sign = sgn;
+  da.dgrad = dgrad;
+  da.dlap = dlap;
+  da.minv = store ? st->minv : nullptr;
+  da.env = store ? st->env : nullptr;
+  da.status = c->d_status;
+  da.flagged = c->d_flagged;
+  da.pivot_tau = c->pivot_tau;
+  da.force64 = c->force64;
+  da.nss = nss;
+  {
+    double fl = 0.0;
+    for (int sp = 0; sp < 2; ++sp) {
+      const double ns = sp == 0 ? t.n_up : t.n_down;
+      fl += 2.0 * ns * ns * ns * 3.0 * n;
+    }
+    Prof pd(c, tangent ? FN_KC_DET_TANGENT : FN_KC_COUNT, fl * Bc * K);
+    launch_det(s, da);
+  }
+  launch_combine(s, logdet, sgn, dgrad, dlap, x, Bc, w0, n, K, N, g, tangent, out.logpsi, out.sign, out.eloc,
+                 out.kinetic, store ? st->wdet : nullptr, c->d_status);
+}
+
+// Adjoint over one chunk: grad64 += sum_w seeds[w] d log|psi_w| / d theta.
+void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const float* seeds, double* grad) {
+  const fn_net& t = c->net;
+  const int n = c->n, N = c->N, L = t.n_layers, K = t.n_det, d1 = t.d1, d2 = t.d2;
+  const long Ktot = (long)K * n, rows = Bc * n, pairs = Bc * n * n;
+  Stored st;
+  float* lp = ar.get<float>(Bc);
+  forward(c, ar, x, Bc, w0, false, true, FwdOut{lp, nullptr, nullptr, nullptr}, &st);
+  const int max_din1 = std::max(4 * N, d1), max_din2 = std::max(4, d2);
+  float* Obar = ar.get<float>(rows * Ktot);
+  float* envg = ar.get<float>(Bc * 2 * Ktot * N);
+  float* Hbar[2] = {ar.get<float>(rows * max_din1), ar.get<float>(rows * max_din1)};
+  float* Zbar = ar.get<float>(rows * d1);
+  float* Ebar[2] = {ar.get<float>(pairs * max_din2), ar.get<float>(pairs * max_din2)};
+  float* Z2bar = ar.get<float>(pairs * d2);
+  float* S = ar.get<float>(Bc * d1);
+  float* M1bar = ar.get<float>(Bc * 2 * max_din1);
+  float* M2bar = ar.get<float>(rows * 2 * max_din2);
+  // scratch for split-K partials and column sums
+  long tn_max = 0, cs_max = 0;
+  auto tn_need = [&](long M, long Nn, long Kk) {
+    tn_max = std::max(tn_max, (long)gemm_tn_splits(M, Nn, Kk) * M * Nn);
+  };
+  auto cs_need = [&](long r, long cl) { cs_max = std::max(cs_max, colsum_scratch_elems(r, cl)); };
+  tn_need(Ktot, d1, rows);
+  cs_need(Bc, 2 * Ktot * N);
+  cs_need(rows, Ktot);
+  for (int l = 0; l < L; ++l) {
+    const int a1 = din1_of(t, l), a2 = din2_of(t, l);
+    tn_need(d2, a2, pairs);
+    cs_need(pairs, d2);
+    tn_need(d1, a1, rows);
+    tn_need(d1, 2 * a2, rows);
+    tn_need(d1, 2 * a1, Bc);
+    cs_need(rows, d1);
+  }
+  float* tn_scr = ar.get<float>(tn_max);
+  double* cs_scr = ar.get<double>(cs_max);
+  if (ar.measure) return;
+
+  cudaStream_t s = c->stream;
+  const float* P = c->d_params;
+  const Layout& Lo = c->lay;
+  auto TN = [&](long M, long Nn, long Kk, const float* A, long lda, const float* Bm, long ldb, double* gdst,
+                long ldg) {
+    gemm_tn_accum(s, M, Nn, Kk, A, lda, Bm, ldb, gdst, ldg, tn_scr, gemm_tn_splits(M, Nn, Kk));
+  };
+  cudaMemsetAsync(Obar, 0, sizeof(float) * rows * Ktot, s);
+  AdjDetArgs ad{};
+  ad.O = st.O;
+  ad.minv = st.minv;
+  ad.env = st.env;
+  ad.wdet = st.wdet;
+  ad.seeds = seeds;
+  ad.x = x;
+  ad.g = geo_of(c);
+  ad.w0 = w0;
+  ad.Bc = Bc;
+  ad.n = n;
+  ad.n_up = t.n_up;
+  ad.K = K;
+  ad.N = N;
+  ad.NS = c->ns_max;
+  ad.pi[0] = P + Lo.pi[0];
+  ad.pi[1] = P + Lo.pi[1];
+  ad.sigma[0] = P + Lo.sigma[0];
+  ad.sigma[1] = P + Lo.sigma[1];
+  ad.Obar = Obar;
+  ad.envgrad = envg;
+  launch_adj_det(s, ad);
+  launch_colsum_accum(s, envg, Bc, 2 * Ktot * N, 2 * Ktot * N, grad + Lo.pi[0], cs_scr);
+  TN(Ktot, d1, rows, Obar, Ktot, st.H[L], d1, grad + Lo.w_orb, d1);
+  launch_colsum_accum(s, Obar, rows, Ktot, Ktot, grad + Lo.g_orb, cs_scr);
+  gemm_nn(s, rows, d1, Ktot, Obar, Ktot, P + Lo.w_orb, d1, Hbar[0], d1, Epi{});
+  int hb = 0, eb = 0;
+  float* Enext = nullptr;
+  for (int l = L - 1; l >= 0; --l) {
+    const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
+    const float* V = P + Lo.V[l];
+    float* Ecur = Ebar[eb];
+    if (l < L - 1) {
+      launch_tanh_bwd(s, Enext, st.Y2[l], pairs, d2, Z2bar);
+      TN(d2, a2, pairs, Z2bar, d2, st.E[l], a2, grad + Lo.W[l], a2);
+      launch_colsum_accum(s, Z2bar, pairs, d2, d2, grad + Lo.c[l], cs_scr);
+      gemm_nn(s, pairs, a2, d2, Z2bar, d2, P + Lo.W[l], a2, Ecur, a2, Epi{});
+      if (l >= 1) launch_add(s, Ecur, Enext, pairs * a2);
+    } else {
+      cudaMemsetAsync(Ecur, 0, sizeof(float) * pairs * a2, s);
+    }
+    float* Hcur = Hbar[hb];
+    launch_tanh_bwd(s, Hcur, st.Y[l], rows, d1, Zbar);
+    TN(d1, a1, rows, Zbar, d1, st.H[l], a1, grad + Lo.V[l], wV);
+    TN(d1, 2 * a2, rows, Zbar, d1, st.M2[l], 2 * a2, grad + Lo.V[l] + 3 * a1, wV);
+    launch_walker_sum(s, Zbar, Bc, n, d1, S);
+    TN(d1, 2 * a1, Bc, S, d1, st.M1[l], 2 * a1, grad + Lo.V[l] + a1, wV);
+    launch_colsum_accum(s, Zbar, rows, d1, d1, grad + Lo.b[l], cs_scr);
+    if (l >= 1) {
+      float* Hprev = Hbar[hb ^ 1];
+      gemm_nn(s, rows, a1, d1, Zbar, d1, V, wV, Hprev, a1, Epi{});
+      launch_add(s, Hprev, Hcur, rows * a1);
+      gemm_nn(s, Bc, 2 * a1, d1, S, d1, V + a1, wV, M1bar, 2 * a1, Epi{});
+      launch_spread_mean1(s, M1bar, Bc, n, t.n_up, a1, Hprev);
+      gemm_nn(s, rows, 2 * a2, d1, Zbar, d1, V + 3 * a1, wV, M2bar, 2 * a2, Epi{});
+      launch_spread_mean2(s, M2bar, Bc, n, t.n_up, a2, Ecur);
+      hb ^= 1;
+    }
+    Enext = Ecur;
+    eb ^= 1;
+  }
+}
+
+size_t ws_bytes(fn_ctx* c, long Bc, int mode) {
+  Arena ar;
+  ar.measure = true;
+  if (mode == 0) forward(c, ar, nullptr, Bc, 0, false, false, FwdOut{}, nullptr);
+  if (mode == 1) forward(c, ar, nullptr, Bc, 0, true, false, FwdOut{}, nullptr);
+  if (mode == 2) vjp_chunk(c, ar, nullptr, Bc, 0, nullptr, nullptr);
+  return ar.off;
+}
+
+// Largest chunk whose workspace fits the budget (FERMINET_WS_GB, default 24).
+long chunk_for(fn_ctx* c, long B, int mode) {
+  double gb = 24.0;
+  if (const char* v = getenv("FERMINET_WS_GB")) gb = atof(v);
+  const double budget = gb * (1ull << 30);
+  const double b1 = (double)ws_bytes(c, 1, mode), b2 = (double)ws_bytes(c, 2, mode);
+  const double per = std::max(1.0, b2 - b1), base = std::max(0.0, b1 - per);
+  long ch = (long)((budget - base) / per);
+  if (ch < 1) ch = 1;
+  if (ch > B) ch = B;
+  if (const char* v = getenv("FERMINET_CHUNK")) {
+    long f = atol(v);
+    if (f > 0 && f < ch) ch = f;
+  }
+  return ch;
+}
+
+fn_status ensure_ws(fn_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_size) return FN_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->ws) cudaFree(c->ws);
+  c->ws = nullptr;
+  c->ws_size = 0;
+  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, FN_ENOMEM, "workspace allocation failed");
+  }
+  c->ws_size = bytes;
+  return FN_OK;
+}
+
+fn_status ensure_aux(fn_ctx* c, long B) {
+  if (B <= c->aux_cap) return FN_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->aux) cudaFree(c->aux);
+  c->aux = nullptr;
+  c->aux_cap = 0;
+  size_t bytes = (size_t)B * (3 * c->n + 4) * sizeof(float);
+  if (cudaMalloc(&c->aux, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, FN_ENOMEM, "auxiliary allocation failed");
+  }
+  c->aux_cap = B;
+  return FN_OK;
+}
+
+fn_status check_batch(fn_ctx* c, const void* x, long B) {
+  if (!x && B > 0) return fail(c, FN_EINVAL, "null walker pointer");
+  if (B < 0) return fail(c, FN_EINVAL, "negative batch size");
+  if (c->G > 1 && B != c->geo_total)
+    return fail(c, FN_EINVAL, "batch size must equal the walker total of the geometry table");
+  return FN_OK;
+}
+
+fn_status after_launch(fn_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "kernel launch");
+  c->err.clear();
+  return FN_OK;
+}
+
+// Runs `mode` passes (0 value, 1 tangent) over the batch in chunks.
+fn_status run_passes(fn_ctx* c, const float* x, long B, bool tangent, const FwdOut& out) {
+  if (B == 0) return FN_OK;
+  const int mode = tangent ? 1 : 0;
+  const long ch = chunk_for(c, B, mode);
+  fn_status st = ensure_ws(c, ws_bytes(c, ch, mode));
+  if (st != FN_OK) return st;
+  const long n3 = 3L * c->n;
+  for (long w0 = 0; w0 < B; w0 += ch) {
+    const long Bc = std::min(ch, B - w0);
+    Arena ar;
+    ar.measure = false;
+    ar.base = c->ws;
+    FwdOut o;
+    o.logpsi = out.logpsi ? out.logpsi + w0 : nullptr;
+    o.sign = out.sign ? out.sign + w0 : nullptr;
+    o.eloc = out.eloc ? out.eloc + w0 : nullptr;
+    o.kinetic = out.kinetic ? out.kinetic + w0 : nullptr;
+    Prof pv(c, tangent ? FN_KC_COUNT : FN_KC_VALUE_PASS, 0.0);
+    forward(c, ar, x + w0 * n3, Bc, w0, tangent, false, o, nullptr);
+  }
+  return after_launch(c);
+}
+
+fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* grad) {
+  cudaStream_t s = c->stream;
+  launch_zero_d(s, c->d_grad64, c->lay.total);
+  if (B > 0) {
+    const long ch = chunk_for(c, B, 2);
+    fn_status st = ensure_ws(c, ws_bytes(c, ch, 2));
+    if (st != FN_OK) return st;
+    const long n3 = 3L * c->n;
+    for (long w0 = 0; w0 < B; w0 += ch) {
+      const long Bc = std::min(ch, B - w0);
+      Arena ar;
+      ar.measure = false;
+      ar.base = c->ws;
+      Prof pa(c, FN_KC_ADJOINT, 0.0);
+      vjp_chunk(c, ar, x + w0 * n3, Bc, w0, seeds + w0, c->d_grad64);
+    }
+  }
+  launch_d2f(s, c->d_grad64, grad, c->lay.total);
+  return after_launch(c);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms, fn_precision prec, void* stream,
+                        fn_ctx** out) {
+  if (!out) return FN_EINVAL;
+  *out = nullptr;
+  if (!net || !geoms || n_geoms < 1) return FN_EINVAL;
+  const fn_net& t = *net;
+  if (t.n_layers < 1 || t.n_layers > 16 || t.d1 < 1 || t.d2 < 1 || t.d2 > 32 || t.n_det < 1 || t.n_up < 0 ||
+      t.n_down < 0 || t.n_up + t.n_down < 1 || t.n_up > 32 || t.n_down > 32 || t.n_nuc < 1)
+    return FN_EINVAL;
+  if (prec != FN_PREC_FP32 && prec != FN_PREC_MIXED) return FN_EINVAL;
+  for (int g = 0; g < n_geoms; ++g)
+    if (!geoms[g].R || !geoms[g].Z) return FN_EINVAL;
+  fn_ctx* c = new fn_ctx();
+  c->net = t;
+  c->n = t.n_up + t.n_down;
+  c->N = t.n_nuc;
+  c->G = n_geoms;
+  c->Ct = tangent_cols(c->n);
+  c->prec = prec;
+  c->stream = (cudaStream_t)stream;
+  c->ns_max = std::max(t.n_up, t.n_down);
+  if (const char* v = getenv("FERMINET_PIVOT_TAU")) c->pivot_tau = (float)atof(v);
+  if (const char* v = getenv("FERMINET_DET64")) c->force64 = atoi(v) != 0;
+  build_layout(t, &c->lay);
+  // geometry table
+  if (n_geoms > 1) {
+    std::vector<std::pair<long, long>> r;
+    for (int g = 0; g < n_geoms; ++g) r.push_back({geoms[g].walker_offset, geoms[g].walker_count});
+    long expect = 0;
+    for (int g = 0; g < n_geoms; ++g) {
+      if (r[g].first != expect || r[g].second < 0) {
+        delete c;
+        return FN_EINVAL;
+      }
+      expect += r[g].second;
+    }
+    c->geo_total = expect;
+  }
+  std::vector<float> R((size_t)n_geoms * c->N * 3), Z((size_t)n_geoms * c->N);
+  std::vector<double> Enn(n_geoms);
+  std::vector<long> off(n_geoms), cnt(n_geoms);
+  std::vector<int> geo(std::max<long>(c->geo_total, 1));
+  for (int g = 0; g < n_geoms; ++g) {
+    double e = 0.0;
+    for (int I = 0; I < c->N; ++I) {
+      for (int a = 0; a < 3; ++a) R[((size_t)g * c->N + I) * 3 + a] = (float)geoms[g].R[3 * I + a];
+      Z[(size_t)g * c->N + I] = (float)geoms[g].Z[I];
+      for (int J = 0; J < I; ++J) {
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          double d = geoms[g].R[3 * I + a] - geoms[g].R[3 * J + a];
+          d2 += d * d;
+        }
+        e += geoms[g].Z[I] * geoms[g].Z[J] / std::sqrt(d2);
+      }
+    }
+    Enn[g] = e;
+    off[g] = geoms[g].walker_offset;
+    cnt[g] = geoms[g].walker_count;
+    if (n_geoms > 1)
+      for (long w = 0; w < cnt[g]; ++w) geo[off[g] + w] = g;
+  }
+  auto bad = [&](cudaError_t e) {
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ferminet_destroy(c);
+      return true;
+    }
+    return false;
+  };
+  if (bad(cudaGetDevice(&c->device))) return FN_ECUDA;
+  if (bad(cudaMalloc(&c->d_params, sizeof(float) * std::max<long>(c->lay.total, 1)))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_grad64, sizeof(double) * std::max<long>(c->lay.total, 1)))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_R, sizeof(float) * R.size()))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_Z, sizeof(float) * Z.size()))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_Enn64, sizeof(double) * n_geoms))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_geo, sizeof(int) * geo.size()))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_geo_off, sizeof(long) * n_geoms))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_geo_cnt, sizeof(long) * n_geoms))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_status, sizeof(unsigned)))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_flagged, sizeof(unsigned long long)))) return FN_ENOMEM;
+  if (bad(cudaMemset(c->d_params, 0, sizeof(float) * std::max<long>(c->lay.total, 1)))) return FN_ECUDA;
+  if (bad(cudaMemcpy(c->d_R, R.data(), sizeof(float) * R.size(), cudaMemcpyHostToDevice))) return FN_ECUDA;
+  if (bad(cudaMemcpy(c->d_Z, Z.data(), sizeof(float) * Z.size(), cudaMemcpyHostToDevice))) return FN_ECUDA;
+  if (bad(cudaMemcpy(c->d_Enn64, Enn.data(), sizeof(double) * n_geoms, cudaMemcpyHostToDevice))) return FN_ECUDA;
+  if (bad(cudaMemcpy(c->d_geo, geo.data(), sizeof(int) * geo.size(), cudaMemcpyHostToDevice))) return FN_ECUDA;
+  if (bad(cudaMemcpy(c->d_geo_off, off.data(), sizeof(long) * n_geoms, cudaMemcpyHostToDevice))) return FN_ECUDA;
+  if (bad(cudaMemcpy(c->d_geo_cnt, cnt.data(), sizeof(long) * n_geoms, cudaMemcpyHostToDevice))) return FN_ECUDA;
+  if (bad(cudaMemset(c->d_status, 0, sizeof(unsigned)))) return FN_ECUDA;
+  if (bad(cudaMemset(c->d_flagged, 0, sizeof(unsigned long long)))) return FN_ECUDA;
+  *out = c;
+  return FN_OK;
+}
+
+fn_status ferminet_param_layout(const fn_ctx* c, fn_param_entry* out, int max_entries, int* n_entries,
+                                long* n_params) {
+  if (!c) return FN_EINVAL;
+  const int ne = (int)c->lay.entries.size();
+  if (out)
+    for (int i = 0; i < ne && i < max_entries; ++i) out[i] = c->lay.entries[i];
+  if (n_entries) *n_entries = ne;
+  if (n_params) *n_params = c->lay.total;
+  return FN_OK;
+}
+
+fn_status ferminet_net_layout(const fn_net* net, fn_param_entry* out, int max_entries, int* n_entries,
+                              long* n_params) {
+  if (!net || net->n_layers < 1 || net->n_layers > 16 || net->d1 < 1 || net->d2 < 1 || net->n_det < 1 ||
+      net->n_up < 0 || net->n_down < 0 || net->n_up + net->n_down < 1 || net->n_nuc < 1)
+    return FN_EINVAL;
+  Layout L;
+  build_layout(*net, &L);
+  const int ne = (int)L.entries.size();
+  if (out)
+    for (int i = 0; i < ne && i < max_entries; ++i) out[i] = L.entries[i];
+  if (n_entries) *n_entries = ne;
+  if (n_params) *n_params = L.total;
+  return FN_OK;
+}
+
+fn_status ferminet_set_params(fn_ctx* c, const float* d_params) {
+  if (!c) return FN_EINVAL;
+  if (!d_params) return fail(c, FN_EINVAL, "null parameter pointer");
+  CK(cudaMemcpyAsync(c->d_params, d_params, sizeof(float) * c->lay.total, cudaMemcpyDeviceToDevice, c->stream));
+  c->err.clear();
+  return FN_OK;
+}
+
+fn_status ferminet_logpsi(fn_ctx* c, const float* d_x, long B, float* d_logpsi, float* d_sign) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (!d_logpsi && B > 0) return fail(c, FN_EINVAL, "null logpsi pointer");
+  return run_passes(c, d_x, B, false, FwdOut{d_logpsi, d_sign, nullptr, nullptr});
+}
+
+fn_status ferminet_local_energy(fn_ctx* c, const float* d_x, long B, float* d_eloc, float* d_logpsi, float* d_sign,
+                                float* d_kinetic) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (!d_eloc && B > 0) return fail(c, FN_EINVAL, "null eloc pointer");
+  return run_passes(c, d_x, B, true, FwdOut{d_logpsi, d_sign, d_eloc, d_kinetic});
+}
+
+fn_status ferminet_logpsi_vjp(fn_ctx* c, const float* d_x, long B, const float* d_seeds, float* d_grad) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (!d_grad || (!d_seeds && B > 0)) return fail(c, FN_EINVAL, "null seeds or grad pointer");
+  return run_vjp(c, d_x, B, d_seeds, d_grad);
+}
+
+fn_status ferminet_energy_grad(fn_ctx* c, const float* d_x, long B, const float* d_eloc, double* d_emean,
+                               float* d_grad) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (!d_grad || !d_emean || (!d_eloc && B > 0)) return fail(c, FN_EINVAL, "null eloc, emean or grad pointer");
+  st = ensure_aux(c, std::max<long>(B, 1));
+  if (st != FN_OK) return st;
+  float* seeds = c->aux;
+  const long B1 = c->G > 1 ? 0 : B;
+  launch_emean(c->stream, d_eloc, c->G, c->d_geo_off, c->d_geo_cnt, B1, d_emean);
+  launch_seeds(c->stream, d_eloc, B, c->G > 1 ? c->d_geo : nullptr, d_emean, c->d_geo_cnt, B1, seeds);
+  return run_vjp(c, d_x, B, seeds, d_grad);
+}
+
+fn_status ferminet_mcmc_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_steps, float width, uint64_t seed,
+                             uint64_t counter, int* d_accepted) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (!d_logpsi && B > 0) return fail(c, FN_EINVAL, "null logpsi pointer");
+  if (n_steps < 0 || !(width >= 0.f)) return fail(c, FN_EINVAL, "bad step count or width");
+  if (B == 0) return FN_OK;
+  st = ensure_aux(c, B);
+  if (st != FN_OK) return st;
+  const int n3 = 3 * c->n;
+  float* xp = c->aux;
+  float* lpp = c->aux + (size_t)B * n3;
+  if (d_accepted) CK(cudaMemsetAsync(d_accepted, 0, sizeof(int) * B, c->stream));
+  for (int s = 0; s < n_steps; ++s) {
+    const uint64_t tc = counter + (uint64_t)s;
+    launch_propose(c->stream, d_x, xp, B, n3, width, seed, tc);
+    st = run_passes(c, xp, B, false, FwdOut{lpp, nullptr, nullptr, nullptr});
+    if (st != FN_OK) return st;
+    launch_accept(c->stream, d_x, xp, d_logpsi, lpp, B, n3, seed, tc, d_accepted);
+  }
+  return after_launch(c);
+}
+
+fn_status ferminet_sync(fn_ctx* c) {
+  if (!c) return FN_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+  if (st & ST_SINGULAR) return fail(c, FN_ESINGULAR, "singular orbital matrix");
+  if (st & ST_NONFINITE) return fail(c, FN_ENONFINITE, "non-finite walker output");
+  if (st & ST_TIMEOUT) return fail(c, FN_ETIMEOUT, "device wait timed out");
+  return FN_OK;
+}
+
+long ferminet_flagged_matrices(fn_ctx* c) {
+  if (!c) return -1;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
+  unsigned long long v = 0;
+  if (cudaMemcpy(&v, c->d_flagged, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  cudaMemset(c->d_flagged, 0, sizeof v);
+  return (long)v;
+}
+
+fn_status ferminet_profile(fn_ctx* c, int enable) {
+  if (!c) return FN_EINVAL;
+  drain_profile(c);
+  for (int k = 0; k < FN_KC_COUNT; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+    c->prof_flops[k] = 0.0;
+  }
+  c->prof_on = enable != 0;
+  return FN_OK;
+}
+
+fn_status ferminet_profile_read(fn_ctx* c, int kc, double* total_ms, long* launches, double* alg_flops) {
+  if (!c || kc < 0 || kc >= FN_KC_COUNT) return FN_EINVAL;
+  drain_profile(c);
+  if (total_ms) *total_ms = c->prof_ms[kc];
+  if (launches) *launches = c->prof_n[kc];
+  if (alg_flops) *alg_flops = c->prof_flops[kc];
+  return FN_OK;
+}
+
+long long ferminet_launch_count(void) { return fn::g_launches.load(); }
+
+const char* ferminet_last_error(const fn_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void ferminet_destroy(fn_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_params);
+  cudaFree(c->d_grad64);
+  cudaFree(c->d_R);
+  cudaFree(c->d_Z);
+  cudaFree(c->d_Enn64);
+  cudaFree(c->d_geo);
+  cudaFree(c->d_geo_off);
+  cudaFree(c->d_geo_cnt);
+  cudaFree(c->d_status);
+  cudaFree(c->d_flagged);
+  cudaFree(c->ws);
+  cudaFree(c->aux);
+  drain_profile(c);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// Library-internal declarations shared by the translation units of libferminet.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/ferminet.h"
+
+namespace fn {
+
+// Columns of a one-electron activation row in the tangent (local-energy) pass:
+//   c = 0            value
+//   c = 1 + 3 e + d  d/d x_{e,d} (electron e, component d)
+//   c = 3 n + 1      Laplacian over all 3n coordinates
+//   c > 3 n + 1      zero padding up to a multiple of 8
+// The value pass uses a single column.
+inline int tangent_cols(int n) { return ((3 * n + 2 + 7) / 8) * 8; }
+// Two-electron rows carry Q = 5 quantities in the tangent pass: value,
+// d/d r_i (3 components; d/d r_j is its negative) and the Laplacian over all
+// coordinates; Q = 1 in the value pass.
+constexpr int kQ = 5;
+
+// Kernels launched by the library (every launch site adds one).
+extern std::atomic<long long> g_launches;
+#define FN_COUNT(n) (::fn::g_launches.fetch_add((n), std::memory_order_relaxed))
+
+// Device status bits.
+enum : unsigned { ST_SINGULAR = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
+
+// ---------------------------------------------------------------------------
+// Parameter offsets (same layout as ferminet_param_layout documents).
+struct Layout {
+  long V[16], b[16], W[16], c[16];
+  long w_orb, g_orb, pi[2], sigma[2];
+  long total;
+  std::vector<fn_param_entry> entries;
+};
+void build_layout(const fn_net& t, Layout* L);
+
+inline int din1_of(const fn_net& t, int l) { return l == 0 ? 4 * t.n_nuc : t.d1; }
+inline int din2_of(const fn_net& t, int l) { return l == 0 ? 4 : t.d2; }
+
+// ---------------------------------------------------------------------------
+// GEMM (FP32 SIMT): C[M][N] = A * B (+ epilogue).
+struct Epi {
+  float beta = 0.f;                 // C = acc + beta * C
+  const float* bias = nullptr;      // + bias[n] on rows with r % bias_period == 0
+  int bias_period = 1;
+  const float* U = nullptr;         // + U[((r / u_div) * u_mul + r % u_mod) * ldu + n]
+  long u_div = 1, u_mul = 1, u_mod = 1, ldu = 0;
+  int act = 0;                      // 1: tanh after the above (value pass only)
+  const float* res = nullptr;       // + res[r * ldr + n] after the activation
+  long ldr = 0;
+};
+// A [M][K] (lda), B [N][K] (ldb):  C = A B^T
+void gemm_nt(cudaStream_t s, long M, long N, long K, const float* A, long lda, const float* B, long ldb, float* C,
+             long ldc, const Epi& e);
+// A [M][K] (lda), B [K][N] (ldb):  C = A B
+void gemm_nn(cudaStream_t s, long M, long N, long K, const float* A, long lda, const float* B, long ldb, float* C,
+             long ldc, const Epi& e);
+// A [K][M] (lda), B [K][N] (ldb):  partial[z] = A^T B over the z-th K slice,
+// then grad[m * ldg + n] += sum_z partial[z] in FP64.  scratch holds
+// splits * M * N floats.
+void gemm_tn_accum(cudaStream_t s, long M, long N, long K, const float* A, long lda, const float* B, long ldb,
+                   double* grad, long ldg, float* scratch, int splits);
+int gemm_tn_splits(long M, long N, long K);
+
+// ---------------------------------------------------------------------------
+// Network kernels (k_network.cu)
+struct Geo {
+  const float* R;      // [G][N][3]
+  const float* Z;      // [G][N]
+  const double* Enn;   // [G] nuclear repulsion
+  const int* geo;      // [B_total] or nullptr (all geometry 0)
+};
+void launch_features(cudaStream_t s, const float* x, long Bc, long w0, int n, int N, int C, int Q, Geo g,
+                     float* H0, float* E0);
+void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int C, int din, float* M1);
+void launch_mean2(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C, float* M2);
+void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, int n, int C, int d1, float* Hout,
+                    float* Y);
+void launch_two_layer(cudaStream_t s, const float* Ein, long Bc, int n, int Q, int din2, int d2, const float* W,
+                      const float* c, bool residual, float* Eout, float* Y2);
+
+// ---------------------------------------------------------------------------
+// Determinants (k_det.cu)
+struct DetArgs {
+  const float* O;      // orbitals [Bc][n][C][Ktot]
+  long ldo;            // Ktot = K * n
+  int C, n, n_up, K, N;
+  const float* x;      // chunk walkers [Bc][n][3]
+  Geo g;
+  long w0, Bc;
+  const float* pi[2];
+  const float* sigma[2];
+  bool tangent;
+  float* logdet;       // [Bc][K][2]
+  float* sign;         // [Bc][K][2]
+  float* dgrad;        // [Bc][K][2][3n]   (tangent)
+  float* dlap;         // [Bc][K][2]       (tangent)
+  float* minv;         // [Bc][K][2][ns*ns] inverses (value pass, optional)
+  float* env;          // [Bc][K][2][ns*ns] envelopes (value pass, optional)
+  unsigned* status;
+  unsigned long long* flagged;
+  float pivot_tau;
+  long nss;            // stride between stored matrices (ns_max^2)
+  int force64;         // redo every matrix in FP64 (diagnostics)
+};
+void launch_det(cudaStream_t s, const DetArgs& a);
+
+// ---------------------------------------------------------------------------
+// Energies, Metropolis, reductions (k_energy.cu)
+void launch_combine(cudaStream_t s, const float* logdet, const float* sign, const float* dgrad, const float* dlap,
+                    const float* x, long Bc, long w0, int n, int K, int N, Geo g, bool tangent, float* logpsi,
+                    float* psign, float* eloc, float* kinetic, float* wdet, unsigned* status);
+void launch_propose(cudaStream_t s, const float* x, float* xp, long B, int n3, float width, uint64_t seed,
+                    uint64_t t);
+void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, const float* lp_prop, long B, int n3,
+                   uint64_t seed, uint64_t t, int* accepted);
+// With G == 1 the single geometry holds all B walkers (B1 = B); otherwise the
+// device tables d_off / d_cnt give each geometry's walker range.
+void launch_emean(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
+                  double* emean);
+void launch_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
+                  const long* d_cnt, long B1, float* seeds);
+void launch_d2f(cudaStream_t s, const double* a, float* b, long n);
+void launch_fill(cudaStream_t s, float* p, float v, long n);
+void launch_zero_d(cudaStream_t s, double* p, long n);
+
+// ---------------------------------------------------------------------------
+// Adjoint kernels (k_adjoint.cu)
+struct AdjDetArgs {
+  const float* O;        // value-pass orbitals [Bc][n][Ktot]
+  const float* minv;     // [Bc][K][2][NS*NS]
+  const float* env;      // [Bc][K][2][NS*NS]
+  const float* wdet;     // [Bc][K]  psi_k / psi
+  const float* seeds;    // [Bc]
+  const float* x;        // chunk walkers [Bc][n][3]
+  Geo g;
+  long w0, Bc;
+  int n, n_up, K, N, NS;
+  const float* pi[2];
+  const float* sigma[2];
+  float* Obar;           // [Bc][n][Ktot]
+  float* envgrad;        // per walker [Bc][2][K*n*N] (pi part then sigma part)
+};
+void launch_adj_det(cudaStream_t s, const AdjDetArgs& a);
+// grad[c] += sum_r X[r * ldx + c] in FP64 (two-pass, deterministic);
+// scratch holds colsum_scratch_elems(rows, cols) doubles.
+long colsum_scratch_elems(long rows, long cols);
+void launch_colsum_accum(cudaStream_t s, const float* X, long rows, long cols, long ldx, double* grad,
+                         double* scratch);
+void launch_tanh_bwd(cudaStream_t s, const float* hbar, const float* Y, long rows, int d, float* zbar);
+void launch_walker_sum(cudaStream_t s, const float* X, long Bc, int n, int d, float* S);
+void launch_spread_mean1(cudaStream_t s, const float* m1bar, long Bc, int n, int n_up, int din, float* hbar);
+void launch_spread_mean2(cudaStream_t s, const float* m2bar, long Bc, int n, int n_up, int din2, float* ebar);
+void launch_add(cudaStream_t s, float* dst, const float* src, long n);
+
+}  // namespace fn
+
+// ---------------------------------------------------------------------------
+// The context.
+struct fn_ctx {
+  fn_net net{};
+  int n = 0, N = 0, G = 0, Ct = 0;
+  fn_precision prec = FN_PREC_FP32;
+  cudaStream_t stream = nullptr;
+  fn::Layout lay;
+  std::vector<long> geo_off, geo_cnt;
+  long geo_total = 0;
+  // device
+  float* d_params = nullptr;
+  float* d_R = nullptr;
+  float* d_Z = nullptr;
+  int* d_geo = nullptr;
+  long* d_geo_cnt = nullptr;
+  long* d_geo_off = nullptr;
+  double* d_Enn64 = nullptr;
+  unsigned* d_status = nullptr;
+  unsigned long long* d_flagged = nullptr;
+  double* d_grad64 = nullptr;
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  float* aux = nullptr;   // Metropolis proposals / seeds
+  long aux_cap = 0;
+  std::string err;
+  int device = 0;
+  int ns_max = 0;
+  float pivot_tau = 1e-4f;  // FP32 pivot-ratio threshold of the FP64 redo
+  int force64 = 0;
+  // per-class event timing
+  bool prof_on = false;
+  struct Pending {
+    int cls;
+    cudaEvent_t e0, e1;
+    double flops;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[FN_KC_COUNT] = {};
+  long prof_n[FN_KC_COUNT] = {};
+  double prof_flops[FN_KC_COUNT] = {};
+};

@@ -1,0 +1,384 @@
+// Orbital matrices, envelopes and determinants (Eq. 3-4).
+//
+// For determinant k and spin s the n_s x n_s matrix is
+//   A_ij = o_ij * e_ij,   o_ij = w^{ks}_i . h^L_j + g^{ks}_i   (orbital GEMM output)
+//   e_ij = sum_m pi^{ks}_im exp(-|sigma^{ks}_im| |r_j - R_m|)  (isotropic envelope)
+// Each matrix is inverted by one warp (Gauss-Jordan with partial pivoting, one
+// row per lane, rows exchanged with shuffles), giving sign, log|det| and A^-1.
+// In the tangent pass the block then forms, for every coordinate c,
+//   d_c log|det A| = tr(A^-1 d_c A)
+//   lap log|det A| = tr(A^-1 lap A) - sum_c tr((A^-1 d_c A)^2),
+// with d_c A and lap A assembled from the orbital columns and the envelope
+// derivatives (product rule; the envelope depends on r_j only).
+#include <math.h>
+
+#include "fn_internal.cuh"
+
+namespace fn {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int geo_of(const Geo& g, long wg) { return g.geo ? g.geo[wg] : 0; }
+
+// Gauss-Jordan inversion of an n x n matrix (n <= NM <= 32) held one row per
+// lane in a[]; b[] starts as the identity row of the lane and ends as the row
+// of A^-1.  Lanes n..NM-1 hold identity padding rows.  All lanes end with the
+// same logabs, sign and pivot extremes.
+template <int NM, class T>
+__device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane, T& logabs, T& sgn, T& pmin,
+                                        T& pmax, bool& sing) {
+  logabs = T(0);
+  sgn = T(1);
+  pmin = T(INFINITY);
+  pmax = T(0);
+  sing = false;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    if (k >= n) break;
+    T v = (lane >= k && lane < n) ? fabs(a[k]) : T(-1);
+    int idx = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      T ov = __shfl_xor_sync(FULL, v, off);
+      int oi = __shfl_xor_sync(FULL, idx, off);
+      if (ov > v || (ov == v && oi < idx)) {
+        v = ov;
+        idx = oi;
+      }
+    }
+    const int p = idx;
+    if (p != k) {
+      const int src = lane == k ? p : (lane == p ? k : lane);
+#pragma unroll
+      for (int c = 0; c < NM; ++c) {
+        a[c] = __shfl_sync(FULL, a[c], src);
+        b[c] = __shfl_sync(FULL, b[c], src);
+      }
+      sgn = -sgn;
+    }
+    const T u = __shfl_sync(FULL, a[k], k);
+    const T au = fabs(u);
+    pmin = fmin(pmin, au);
+    pmax = fmax(pmax, au);
+    if (!(au > T(0))) {
+      sing = true;
+      break;
+    }
+    logabs += log(au);
+    if (u < T(0)) sgn = -sgn;
+    const T iu = T(1) / u;
+    const T fct = a[k];
+#pragma unroll
+    for (int c = 0; c < NM; ++c) {
+      if (c >= k) {
+        T rk = __shfl_sync(FULL, a[c], k) * iu;
+        a[c] = (lane == k) ? rk : fma(-fct, rk, a[c]);
+      }
+      T rb = __shfl_sync(FULL, b[c], k) * iu;
+      b[c] = (lane == k) ? rb : fma(-fct, rb, b[c]);
+    }
+  }
+}
+
+struct MatId {
+  long w;
+  int k, s, ns, j0;
+  long q0;
+};
+
+__device__ __forceinline__ MatId mat_id(long mat, const DetArgs& a) {
+  MatId m;
+  m.w = mat / (2 * a.K);
+  int r = (int)(mat % (2 * a.K));
+  m.k = r / 2;
+  m.s = r % 2;
+  m.ns = m.s == 0 ? a.n_up : a.n - a.n_up;
+  m.j0 = m.s == 0 ? 0 : a.n_up;
+  m.q0 = (m.s == 0 ? 0L : (long)a.K * a.n_up) + (long)m.k * m.ns;
+  return m;
+}
+
+// Envelope of orbital i at electron jg, with its gradient along r_jg and its
+// Laplacian, in precision T.
+template <class T>
+__device__ __forceinline__ void envelope(const DetArgs& a, const MatId& m, int i, int jg, const float* R, T& ev,
+                                         T* eg, T& el, bool deriv) {
+  const float* xj = a.x + (m.w * a.n + jg) * 3;
+  const float* pi = a.pi[m.s] + ((long)m.k * m.ns + i) * a.N;
+  const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + i) * a.N;
+  ev = T(0);
+  el = T(0);
+  eg[0] = eg[1] = eg[2] = T(0);
+  for (int mm = 0; mm < a.N; ++mm) {
+    T d0 = (T)xj[0] - (T)R[3 * mm], d1 = (T)xj[1] - (T)R[3 * mm + 1], d2 = (T)xj[2] - (T)R[3 * mm + 2];
+    T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    T s = fabs((T)sg[mm]);
+    T ex = (T)pi[mm] * exp(-s * r);
+    ev += ex;
+    if (deriv) {
+      T ir = r > T(0) ? T(1) / r : T(0);
+      T gs = -s * ex * ir;
+      eg[0] = fma(gs, d0, eg[0]);
+      eg[1] = fma(gs, d1, eg[1]);
+      eg[2] = fma(gs, d2, eg[2]);
+      el = fma(ex, s * s - T(2) * s * ir, el);
+    }
+  }
+}
+
+// One warp, one matrix, value pass, in precision T.  Writes sign, log|det| and
+// (optionally) the inverse and envelopes; returns whether the pivot ratio
+// flags the matrix as ill-conditioned (warp-uniform).
+template <int NM, class T>
+__device__ bool det_value_body(const DetArgs& a, long mat, const MatId& m, int lane, const float* R,
+                               bool count) {
+  T ra[NM], rb[NM];
+  const long NSS = a.nss;
+#pragma unroll
+  for (int c = 0; c < NM; ++c) {
+    ra[c] = (c == lane) ? T(1) : T(0);
+    rb[c] = (c == lane) ? T(1) : T(0);
+  }
+  if (lane < m.ns) {
+#pragma unroll
+    for (int c = 0; c < NM; ++c) {
+      if (c < m.ns) {
+        const int jg = m.j0 + c;
+        T o = (T)a.O[((m.w * a.n + jg) * (long)a.C) * a.ldo + m.q0 + lane];
+        T ev, eg[3], el;
+        envelope<T>(a, m, lane, jg, R, ev, eg, el, false);
+        ra[c] = o * ev;
+        if (a.env) a.env[mat * NSS + lane * m.ns + c] = (float)ev;
+      }
+    }
+  }
+  T logabs, sgn, pmin, pmax;
+  bool sing;
+  warp_gj<NM, T>(ra, rb, m.ns, lane, logabs, sgn, pmin, pmax, sing);
+  const bool flag = !sing && pmin < (T)a.pivot_tau * pmax;
+  if (lane == 0) {
+    a.logdet[mat] = sing ? -INFINITY : (float)logabs;
+    a.sign[mat] = sing ? 0.f : (float)sgn;
+    if (count) {
+      if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
+      else if (flag) atomicAdd(a.flagged, 1ull);
+    }
+  }
+  if (a.minv && lane < m.ns) {
+#pragma unroll
+    for (int c = 0; c < NM; ++c)
+      if (c < m.ns) a.minv[mat * NSS + lane * m.ns + c] = sing ? 0.f : (float)rb[c];
+  }
+  return flag;
+}
+
+// Value pass: one warp per matrix, four matrices per block; FP64 redo of
+// matrices whose FP32 pivot ratio falls below pivot_tau.
+template <int NM>
+__global__ void __launch_bounds__(128) k_det_value(DetArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long mat = (long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const long nmat = a.Bc * a.K * 2;
+  if (mat >= nmat) return;
+  const MatId m = mat_id(mat, a);
+  if (m.ns == 0) {
+    if (lane == 0) {
+      a.logdet[mat] = 0.f;
+      a.sign[mat] = 1.f;
+    }
+    return;
+  }
+  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
+  const bool flag = det_value_body<NM, float>(a, mat, m, lane, R, true);
+  if (flag || a.force64) det_value_body<NM, double>(a, mat, m, lane, R, false);
+}
+
+template <int NM, class T>
+struct TangentSmem {
+  T Ms[NM][NM + 1];
+  T Os[NM][NM + 1];
+  T Es[NM][NM + 1];
+  T Eg[3][NM][NM + 1];
+  T El[NM][NM + 1];
+  T Xs[128 * NM];
+};
+
+// Tangent-pass body for one matrix in precision T (128 threads).  Returns
+// whether the pivot ratio flags the matrix (block-uniform).
+template <int NM, class T>
+__device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, const float* R, char* raw,
+                                 bool count) {
+  TangentSmem<NM, T>& sm = *reinterpret_cast<TangentSmem<NM, T>*>(raw);
+  __shared__ double red[4];
+  __shared__ int sing_s, flag_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n3 = 3 * a.n;
+  const int ns = m.ns;
+  auto orow = [&](int jg, int c) -> const float* {
+    return a.O + ((m.w * a.n + jg) * (long)a.C + c) * a.ldo + m.q0;
+  };
+  for (int t = tid; t < ns * ns; t += 128) {
+    int i = t / ns, j = t % ns;
+    T ev, eg[3], el;
+    envelope<T>(a, m, i, m.j0 + j, R, ev, eg, el, true);
+    sm.Es[i][j] = ev;
+    sm.Eg[0][i][j] = eg[0];
+    sm.Eg[1][i][j] = eg[1];
+    sm.Eg[2][i][j] = eg[2];
+    sm.El[i][j] = el;
+    sm.Os[i][j] = (T)orow(m.j0 + j, 0)[i];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    T ra[NM], rb[NM];
+#pragma unroll
+    for (int c = 0; c < NM; ++c) {
+      ra[c] = (c == lane) ? T(1) : T(0);
+      rb[c] = (c == lane) ? T(1) : T(0);
+    }
+    if (lane < ns) {
+#pragma unroll
+      for (int c = 0; c < NM; ++c)
+        if (c < ns) ra[c] = sm.Os[lane][c] * sm.Es[lane][c];
+    }
+    T logabs, sgn, pmin, pmax;
+    bool sing;
+    warp_gj<NM, T>(ra, rb, ns, lane, logabs, sgn, pmin, pmax, sing);
+    if (lane < ns) {
+#pragma unroll
+      for (int c = 0; c < NM; ++c)
+        if (c < ns) sm.Ms[lane][c] = rb[c];
+    }
+    if (lane == 0) {
+      const bool flag = !sing && pmin < (T)a.pivot_tau * pmax;
+      a.logdet[mat] = sing ? -INFINITY : (float)logabs;
+      a.sign[mat] = sing ? 0.f : (float)sgn;
+      sing_s = sing ? 1 : 0;
+      flag_s = flag ? 1 : 0;
+      if (count) {
+        if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
+        else if (flag) atomicAdd(a.flagged, 1ull);
+      }
+    }
+  }
+  __syncthreads();
+  const bool flag = flag_s != 0;
+  if (sing_s) {
+    if (tid == 0) a.dlap[mat] = 0.f;
+    for (int c = tid; c < n3; c += 128) a.dgrad[mat * n3 + c] = 0.f;
+    return false;
+  }
+  // tr(A^-1 lap A), lap A_ij = lap o e + o lap e + 2 grad_j o . grad_j e
+  double part = 0.0;
+  for (int t = tid; t < ns * ns; t += 128) {
+    int i = t / ns, j = t % ns, jg = m.j0 + j;
+    T lo = (T)orow(jg, n3 + 1)[i];
+    T cross = (T)orow(jg, 1 + 3 * jg)[i] * sm.Eg[0][i][j] + (T)orow(jg, 2 + 3 * jg)[i] * sm.Eg[1][i][j] +
+              (T)orow(jg, 3 + 3 * jg)[i] * sm.Eg[2][i][j];
+    T la = lo * sm.Es[i][j] + sm.Os[i][j] * sm.El[i][j] + T(2) * cross;
+    part += (double)(sm.Ms[j][i] * la);
+  }
+  // coordinates in batches of cb: X_c = A^-1 d_c A, column j per thread
+  const int cb = 128 / ns;
+  for (int c0 = 0; c0 < n3; c0 += cb) {
+    const int cl = tid / ns, j = tid % ns, c = c0 + cl;
+    if (cl < cb && c < n3) {
+      const int jg = m.j0 + j, e = c / 3, dd = c % 3;
+      const float* od = orow(jg, 1 + c);
+      T col[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        if (i < ns) {
+          T v = (T)od[i] * sm.Es[i][j];
+          if (e == jg) v = fma(sm.Os[i][j], sm.Eg[dd][i][j], v);
+          col[i] = v;
+        } else {
+          col[i] = T(0);
+        }
+      }
+      T* X = sm.Xs + (long)cl * ns * ns;
+      for (int i = 0; i < ns; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int l = 0; l < NM; ++l)
+          if (l < ns) acc = fma(sm.Ms[i][l], col[l], acc);
+        X[i * ns + j] = acc;
+      }
+    }
+    __syncthreads();
+    if (tid < cb && c0 + tid < n3) {
+      const T* X = sm.Xs + (long)tid * ns * ns;
+      T tr = T(0), tr2 = T(0);
+      for (int i = 0; i < ns; ++i) {
+        tr += X[i * ns + i];
+        for (int j2 = 0; j2 < ns; ++j2) tr2 = fma(X[i * ns + j2], X[j2 * ns + i], tr2);
+      }
+      a.dgrad[mat * n3 + c0 + tid] = (float)tr;
+      part -= (double)tr2;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (tid == 0) a.dlap[mat] = (float)(red[0] + red[1] + red[2] + red[3]);
+  __syncthreads();
+  return flag;
+}
+
+// Tangent pass: one 128-thread block per matrix; FP64 redo of matrices whose
+// FP32 pivot ratio falls below pivot_tau.
+template <int NM>
+__global__ void __launch_bounds__(128) k_det_tangent(DetArgs a) {
+  extern __shared__ __align__(16) char raw[];
+  const long mat = blockIdx.x;
+  const MatId m = mat_id(mat, a);
+  const int n3 = 3 * a.n, tid = threadIdx.x;
+  if (m.ns == 0) {
+    if (tid == 0) {
+      a.logdet[mat] = 0.f;
+      a.sign[mat] = 1.f;
+      a.dlap[mat] = 0.f;
+    }
+    for (int c = tid; c < n3; c += 128) a.dgrad[mat * n3 + c] = 0.f;
+    return;
+  }
+  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
+  const bool flag = det_tangent_body<NM, float>(a, mat, m, R, raw, true);
+  if (flag || a.force64) det_tangent_body<NM, double>(a, mat, m, R, raw, false);
+}
+
+template <int NM>
+void launch_nm(cudaStream_t s, const DetArgs& a) {
+  long nmat = a.Bc * a.K * 2;
+  if (nmat <= 0) return;
+  if (a.tangent) {
+    const int smem = (int)sizeof(TangentSmem<NM, double>);
+    static bool attr = false;  // set once per process (the attribute is per function)
+    if (!attr) {
+      cudaFuncSetAttribute(k_det_tangent<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr = true;
+    }
+    FN_COUNT(1), k_det_tangent<NM><<<(unsigned)nmat, 128, smem, s>>>(a);
+  } else {
+    FN_COUNT(1), k_det_value<NM><<<(unsigned)((nmat + 3) / 4), 128, 0, s>>>(a);
+  }
+}
+
+}  // namespace
+
+void launch_det(cudaStream_t s, const DetArgs& a) {
+  int ns = a.n_up > a.n - a.n_up ? a.n_up : a.n - a.n_up;
+  if (ns <= 4)
+    launch_nm<4>(s, a);
+  else if (ns <= 8)
+    launch_nm<8>(s, a);
+  else if (ns <= 16)
+    launch_nm<16>(s, a);
+  else
+    launch_nm<32>(s, a);
+}
+
+}  // namespace fn

@@ -1,0 +1,237 @@
+// Streaming kernels of the permutation-equivariant network: input features,
+// spin-averaged means, the forward-Laplacian tanh step of the one-electron
+// stream and the fused two-electron layer.
+//
+// Forward-Laplacian propagation (Sec. 3 computes the kinetic energy with
+// forward-mode derivatives): every activation carries, besides its value, its
+// derivative along each of the 3n electron coordinates and its Laplacian.  A
+// linear map acts on all columns alike (the bias only on the value); for
+// y = tanh(z):  dy = (1 - y^2) dz,  lap y = (1 - y^2) lap z - 2 y (1 - y^2) |dz|^2.
+#include "fn_internal.cuh"
+
+namespace fn {
+namespace {
+
+__device__ __forceinline__ int geo_of(const Geo& g, long wg) { return g.geo ? g.geo[wg] : 0; }
+
+// h^0_i = [r_i - R_I, |r_i - R_I|]_I, one thread per (walker, electron, column).
+__global__ void k_feat1(const float* __restrict__ x, long Bc, long w0, int n, int N, int C, Geo g,
+                        float* __restrict__ H0) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * n * C;
+  if (idx >= tot) return;
+  int c = (int)(idx % C);
+  long wi = idx / C;
+  int i = (int)(wi % n);
+  long w = wi / n;
+  const float* R = g.R + (long)geo_of(g, w0 + w) * N * 3;
+  const float* xi = x + (w * n + i) * 3;
+  float* out = H0 + idx * 4 * N;
+  const int n3 = 3 * n;
+  for (int I = 0; I < N; ++I) {
+    float d0 = xi[0] - R[3 * I], d1 = xi[1] - R[3 * I + 1], d2 = xi[2] - R[3 * I + 2];
+    float r = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c == 0) {
+      v[0] = d0; v[1] = d1; v[2] = d2; v[3] = r;
+    } else if (c <= n3) {
+      int e = (c - 1) / 3, dd = (c - 1) % 3;
+      if (e == i) {
+        v[dd] = 1.f;
+        float dv = dd == 0 ? d0 : (dd == 1 ? d1 : d2);
+        v[3] = r > 0.f ? dv / r : 0.f;
+      }
+    } else if (c == n3 + 1) {
+      v[3] = r > 0.f ? 2.f / r : 0.f;
+    }
+    *reinterpret_cast<float4*>(out + 4 * I) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// h^0_ij = [r_i - r_j, |r_i - r_j|]; Q = 5 rows (value, d/dr_i xyz, full
+// Laplacian = 2 * (2 / r) for the distance) or Q = 1.  Zero for i = j.
+__global__ void k_feat2(const float* __restrict__ x, long Bc, int n, int Q, float* __restrict__ E0) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * n * n;
+  if (idx >= tot) return;
+  int j = (int)(idx % n);
+  long wi = idx / n;
+  int i = (int)(wi % n);
+  long w = wi / n;
+  float* out = E0 + idx * Q * 4;
+  if (i == j) {
+    for (int q = 0; q < Q * 4; ++q) out[q] = 0.f;
+    return;
+  }
+  const float* xi = x + (w * n + i) * 3;
+  const float* xj = x + (w * n + j) * 3;
+  float d[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+  float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  *reinterpret_cast<float4*>(out) = make_float4(d[0], d[1], d[2], r);
+  if (Q == 1) return;
+  float ir = r > 0.f ? 1.f / r : 0.f;
+  for (int dd = 0; dd < 3; ++dd) {
+    float v[4] = {0.f, 0.f, 0.f, d[dd] * ir};
+    v[dd] = 1.f;
+    *reinterpret_cast<float4*>(out + 4 * (1 + dd)) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  *reinterpret_cast<float4*>(out + 16) = make_float4(0.f, 0.f, 0.f, 4.f * ir);
+}
+
+// M1[w][c][s*din + f] = mean over electrons i of spin s of H[w][i][c][f].
+__global__ void k_mean1(const float* __restrict__ H, long Bc, int n, int n_up, int C, int din,
+                        float* __restrict__ M1) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * C * 2 * din;
+  if (idx >= tot) return;
+  int f = (int)(idx % din);
+  long r = idx / din;
+  int s = (int)(r % 2);
+  long wc = r / 2;
+  int c = (int)(wc % C);
+  long w = wc / C;
+  int i0 = s == 0 ? 0 : n_up, i1 = s == 0 ? n_up : n;
+  float acc = 0.f;
+  for (int i = i0; i < i1; ++i) acc += H[((w * n + i) * C + c) * din + f];
+  M1[idx] = i1 > i0 ? acc / (float)(i1 - i0) : 0.f;
+}
+
+// M2[w][i][c][s*din2 + f]: mean over electrons j of spin s of h_ij, expanded
+// to the dense column layout.  With T the derivative of h_ij along r_i,
+// d/dr_e mean_j h_ij = (1/n_s) sum_j T_ij for e = i, -(1/n_s) T_ie for e != i
+// of spin s, and 0 otherwise; the Laplacian column is the mean of the
+// two-electron Laplacians.
+__global__ void k_mean2(const float* __restrict__ E, long Bc, int n, int n_up, int Q, int din2, int C,
+                        float* __restrict__ M2) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * n * C * 2 * din2;
+  if (idx >= tot) return;
+  int f = (int)(idx % din2);
+  long r = idx / din2;
+  int s = (int)(r % 2);
+  r /= 2;
+  int c = (int)(r % C);
+  long wi = r / C;
+  int i = (int)(wi % n);
+  long w = wi / n;
+  int j0 = s == 0 ? 0 : n_up, j1 = s == 0 ? n_up : n;
+  int ns = j1 - j0;
+  float out = 0.f;
+  if (ns > 0) {
+    const float* Ei = E + (w * n + i) * (long)n * Q * din2;
+    const float inv = 1.f / (float)ns;
+    const int n3 = 3 * n;
+    if (c == 0) {
+      float a = 0.f;
+      for (int j = j0; j < j1; ++j) a += Ei[(long)j * Q * din2 + f];
+      out = a * inv;
+    } else if (Q > 1 && c <= n3) {
+      int e = (c - 1) / 3, dd = (c - 1) % 3;
+      if (e == i) {
+        float a = 0.f;
+        for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 1 + dd) * din2 + f];
+        out = a * inv;
+      } else if (e >= j0 && e < j1) {
+        out = -Ei[((long)e * Q + 1 + dd) * din2 + f] * inv;
+      }
+    } else if (Q > 1 && c == n3 + 1) {
+      float a = 0.f;
+      for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 4) * din2 + f];
+      out = a * inv;
+    }
+  }
+  M2[idx] = out;
+}
+
+// One-electron tanh with forward-Laplacian columns, plus residual.
+__global__ void k_tanh_fl(const float* __restrict__ Z, const float* __restrict__ Hres, long Bc, int n, int C,
+                          int d1, float* __restrict__ Hout, float* __restrict__ Y) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * n * d1;
+  if (idx >= tot) return;
+  int f = (int)(idx % d1);
+  long wi = idx / d1;
+  const long base = wi * C * d1 + f;
+  float z0 = Z[base];
+  float y = tanhf(z0);
+  float s = 1.f - y * y;
+  if (Y) Y[idx] = y;
+  Hout[base] = y + (Hres ? Hres[base] : 0.f);
+  if (C == 1) return;
+  const int n3 = 3 * n;
+  float sq = 0.f;
+  for (int c = 1; c <= n3; ++c) {
+    float zc = Z[base + (long)c * d1];
+    sq = fmaf(zc, zc, sq);
+    Hout[base + (long)c * d1] = s * zc + (Hres ? Hres[base + (long)c * d1] : 0.f);
+  }
+  float zl = Z[base + (long)(n3 + 1) * d1];
+  Hout[base + (long)(n3 + 1) * d1] = s * zl - 2.f * y * s * sq + (Hres ? Hres[base + (long)(n3 + 1) * d1] : 0.f);
+  for (int c = n3 + 2; c < C; ++c) Hout[base + (long)c * d1] = 0.f;
+}
+
+// Two-electron layer h_ij -> tanh(W h_ij + c) (+ h_ij), one thread per
+// (pair, output feature), all Q rows at once.  The Laplacian rule uses
+// |dz|^2 = 2 |dz/dr_i|^2 because dz/dr_j = -dz/dr_i.
+__global__ void k_two_layer(const float* __restrict__ Ein, long Bc, int n, int Q, int din2, int d2,
+                            const float* __restrict__ W, const float* __restrict__ cb, int residual,
+                            float* __restrict__ Eout, float* __restrict__ Y2) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * n * n * d2;
+  if (idx >= tot) return;
+  int f = (int)(idx % d2);
+  long p = idx / d2;
+  const float* in = Ein + p * Q * din2;
+  const float* wr = W + (long)f * din2;
+  float z[kQ] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < din2; ++k) {
+    float wk = wr[k];
+    for (int q = 0; q < Q; ++q) z[q] = fmaf(wk, in[q * din2 + k], z[q]);
+  }
+  z[0] += cb[f];
+  float y = tanhf(z[0]);
+  float s = 1.f - y * y;
+  if (Y2) Y2[idx] = y;
+  float* out = Eout + p * Q * d2;
+  out[f] = y + (residual ? in[f] : 0.f);
+  if (Q == 1) return;
+  float sq = z[1] * z[1] + z[2] * z[2] + z[3] * z[3];
+  for (int q = 1; q <= 3; ++q) out[q * d2 + f] = s * z[q] + (residual ? in[q * din2 + f] : 0.f);
+  out[4 * d2 + f] = s * z[4] - 4.f * y * s * sq + (residual ? in[4 * din2 + f] : 0.f);
+}
+
+inline unsigned nblk(long tot, int bs) { return (unsigned)((tot + bs - 1) / bs); }
+
+}  // namespace
+
+void launch_features(cudaStream_t s, const float* x, long Bc, long w0, int n, int N, int C, int Q, Geo g, float* H0,
+                     float* E0) {
+  long t1 = Bc * n * C;
+  if (t1 > 0) FN_COUNT(1), k_feat1<<<nblk(t1, 256), 256, 0, s>>>(x, Bc, w0, n, N, C, g, H0);
+  long t2 = Bc * n * n;
+  if (t2 > 0) FN_COUNT(1), k_feat2<<<nblk(t2, 256), 256, 0, s>>>(x, Bc, n, Q, E0);
+}
+
+void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int C, int din, float* M1) {
+  long tot = Bc * C * 2 * din;
+  if (tot > 0) FN_COUNT(1), k_mean1<<<nblk(tot, 256), 256, 0, s>>>(H, Bc, n, n_up, C, din, M1);
+}
+
+void launch_mean2(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C, float* M2) {
+  long tot = Bc * n * C * 2 * din2;
+  if (tot > 0) FN_COUNT(1), k_mean2<<<nblk(tot, 256), 256, 0, s>>>(E, Bc, n, n_up, Q, din2, C, M2);
+}
+
+void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, int n, int C, int d1, float* Hout,
+                    float* Y) {
+  long tot = Bc * n * d1;
+  if (tot > 0) FN_COUNT(1), k_tanh_fl<<<nblk(tot, 256), 256, 0, s>>>(Z, Hres, Bc, n, C, d1, Hout, Y);
+}
+
+void launch_two_layer(cudaStream_t s, const float* Ein, long Bc, int n, int Q, int din2, int d2, const float* W,
+                      const float* c, bool residual, float* Eout, float* Y2) {
+  long tot = Bc * n * n * d2;
+  if (tot > 0) FN_COUNT(1), k_two_layer<<<nblk(tot, 256), 256, 0, s>>>(Ein, Bc, n, Q, din2, d2, W, c, residual ? 1 : 0, Eout, Y2);
+}
+
+}  // namespace fn

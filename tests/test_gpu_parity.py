@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every comparison uses the same seeded float32 inputs on both sides.  FP32-path
+bars: log|psi| within 1e-5 relative (to max(|log psi|, 1)) and the local energy
+within 1e-4 Ha per walker and 1e-5 Ha on the batch mean, each widened by the
+FP32 rounding term of helpers.py where the walker sits near a node of psi;
+parameter gradients within 1e-3 relative L2 (FP32 accumulation over walkers
+whose orbital matrices may be ill-conditioned).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_07125_gb300 import synth
+from helpers import (TOL_ELOC_ABS, TOL_LOGPSI_REL, U32, conditioning, gamma, eloc_bound, emean_bound, logpsi_bound, rel_err,
+                     setup)
+
+TOL_GRAD_FP32 = 1e-3
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [("li", None), ("ne", 24), ("ar", 6), ("c4h6", 4), ("c4h4x8", 2)]
+
+
+def make(wl, P, precision="fp32"):
+    from paper_2011_07125_gb300.binding import FermiNet
+    fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision=precision)
+    fn.set_params(torch.from_numpy(P).cuda())
+    return fn
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("name,per", CASES)
+def test_logpsi(name, per):
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P)
+    lp, sg = fn.logpsi(cuda(x))
+    ref = oracle.local_energy(wl.net, P, wl.geoms, x, geo=geo) if per else None
+    lp_o, sg_o = oracle.logpsi(wl.net, P, wl.geoms, x, geo=geo)
+    assert fn.sync() == "FN_OK"
+    d = np.abs(lp.cpu().numpy() - lp_o)
+    print(name, "logpsi max rel err", rel_err(lp.cpu().numpy(), lp_o).max())
+    assert np.array_equal(sg.cpu().numpy(), sg_o)
+    bound = logpsi_bound(wl.net, ref) if ref is not None else TOL_LOGPSI_REL * np.maximum(np.abs(lp_o), 1)
+    assert np.all(d <= bound), (d / bound).max()
+
+
+@pytest.mark.parametrize("name,per", CASES)
+def test_local_energy(name, per):
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P)
+    out = fn.local_energy(cuda(x))
+    ref = oracle.local_energy(wl.net, P, wl.geoms, x, geo=geo)
+    assert fn.sync() == "FN_OK"
+    e = out["eloc"].cpu().numpy().astype(np.float64)
+    de = np.abs(e - ref["eloc"])
+    print(name, "E_L max abs err", de.max(), "mean err", abs(e.mean() - ref["eloc"].mean()),
+          "kinetic err", np.abs(out["kinetic"].cpu().numpy() - ref["kinetic"]).max(),
+          "|E_L| max", np.abs(ref["eloc"]).max())
+    S, _ = conditioning(ref)
+    strict = gamma(wl.net) * U32 * S < 0.1 * TOL_ELOC_ABS  # rounding floor well below the bar
+    print(name, "walkers", len(e), "well-conditioned", int(strict.sum()),
+          "max err there", de[strict].max() if strict.any() else None)
+    assert np.all(np.abs(out["logpsi"].cpu().numpy() - ref["logpsi"]) <= logpsi_bound(wl.net, ref))
+    assert np.array_equal(out["sign"].cpu().numpy(), ref["sign"])
+    bound = eloc_bound(wl.net, ref)
+    assert np.all(de <= bound), (de / bound).max()
+    assert abs(e.mean() - ref["eloc"].mean()) <= emean_bound(wl.net, ref)
+    if strict.any():
+        assert de[strict].max() < TOL_ELOC_ABS
+
+
+def test_chunked_equals_unchunked(monkeypatch):
+    """A ragged split of the batch into chunks changes no bit of any output."""
+    wl, lay, P, x, geo = setup("ne", 23)
+    fn = make(wl, P)
+    xx = cuda(x)
+    a = fn.local_energy(xx)
+    la = fn.logpsi(xx)[0]
+    ga = fn.logpsi_vjp(xx, torch.linspace(-1, 1, 23, device="cuda"))
+    monkeypatch.setenv("FERMINET_CHUNK", "5")
+    b = fn.local_energy(xx)
+    lb = fn.logpsi(xx)[0]
+    gb = fn.logpsi_vjp(xx, torch.linspace(-1, 1, 23, device="cuda"))
+    assert torch.equal(a["eloc"], b["eloc"]) and torch.equal(la, lb)
+    # the FP64 gradient reduction sums per-chunk FP32 partials in another order
+    assert float((ga - gb).norm() / ga.norm()) < 1e-5
+
+
+@pytest.mark.parametrize("name,per", [("li", 16), ("ne", 8), ("c4h6", 2), ("c4h4x8", 1)])
+def test_logpsi_vjp(name, per):
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P)
+    seeds = np.random.default_rng(3).standard_normal(x.shape[0]).astype(np.float32)
+    g = fn.logpsi_vjp(cuda(x), cuda(seeds)).cpu().numpy().astype(np.float64)
+    g_o = oracle.logpsi_vjp(wl.net, P, wl.geoms, x, seeds, geo=geo)
+    err = np.linalg.norm(g - g_o) / np.linalg.norm(g_o)
+    print(name, "vjp rel L2", err)
+    for e in lay:  # block by block, so a misplaced block is named
+        sl = slice(e.offset, e.offset + e.count)
+        nb = np.linalg.norm(g_o[sl])
+        if nb > 1e-6 * np.linalg.norm(g_o):
+            assert np.linalg.norm(g[sl] - g_o[sl]) / nb < 1e-2, e.name
+    assert err < TOL_GRAD_FP32
+
+
+@pytest.mark.parametrize("name,per", [("li", 32), ("c4h4x8", 2)])
+def test_energy_grad(name, per):
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P)
+    eloc = (np.random.default_rng(4).standard_normal(x.shape[0]) * 2 - 7).astype(np.float32)
+    em, g = fn.energy_grad(cuda(x), cuda(eloc))
+    em_o, g_o = oracle.energy_grad(wl.net, P, wl.geoms, x, eloc, geo=geo)
+    np.testing.assert_allclose(em.cpu().numpy(), em_o, rtol=1e-12, atol=1e-12)
+    err = np.linalg.norm(g.cpu().numpy() - g_o) / np.linalg.norm(g_o)
+    print(name, "energy grad rel L2", err)
+    assert err < TOL_GRAD_FP32
+
+
+def test_autograd_function():
+    from paper_2011_07125_gb300.binding import logpsi_autograd
+    wl, lay, P, x, geo = setup("li", 16)
+    fn = make(wl, P)
+    p = cuda(P).requires_grad_(True)
+    xx = cuda(x)
+    lp = logpsi_autograd(fn, p, xx)
+    w = torch.linspace(0.5, 1.5, 16, device="cuda")
+    (lp * w).sum().backward()
+    g_o = oracle.logpsi_vjp(wl.net, P, wl.geoms, x, w.cpu().numpy())
+    err = np.linalg.norm(p.grad.cpu().numpy() - g_o) / np.linalg.norm(g_o)
+    assert err < TOL_GRAD_FP32
+
+
+@pytest.mark.parametrize("steps,width", [(1, 0.02), (4, 0.4)])
+def test_mcmc(steps, width):
+    """Same Philox streams on both sides: identical decisions except where the
+    acceptance margin |2 dlogpsi - log u| is below 1e-4 (precision-dependent
+    near-ties), identical positions for the rest."""
+    wl, lay, P, x, geo = setup("li")
+    fn = make(wl, P)
+    xx = cuda(x)
+    lp = fn.logpsi(xx)[0]
+    lp0 = lp.cpu().numpy().astype(np.float64)
+    acc = fn.mcmc_step(xx, lp, steps, width, synth.SEED_MCMC, 7)
+    xo, lpo, acco, margin = oracle.mcmc(wl.net, P, wl.geoms, x, lp0, steps, width, synth.SEED_MCMC, 7)
+    assert fn.sync() == "FN_OK"
+    ok = margin > 1e-4
+    assert ok.mean() > 0.95
+    a = acc.cpu().numpy()
+    assert np.array_equal(a[ok], acco[ok])
+    dx = np.abs(xx.cpu().numpy() - xo).reshape(len(x), -1).max(axis=1)
+    assert dx[ok].max() < 1e-5
+    assert 0 < a.sum() < steps * len(x) or width < 0.05
+    assert rel_err(lp.cpu().numpy()[ok], lpo[ok]).max() < TOL_LOGPSI_REL
+
+
+def test_hydrogen_exact_on_gpu():
+    net = synth.Net(2, 8, 4, 1, 1, 0, 1)
+    lay = oracle.layout(net)
+    P = synth.init_params(lay, 3)
+    for e in lay:
+        if e.name.startswith("w_orb"):
+            P[e.offset:e.offset + e.count] = 0
+        if e.name.startswith("g_orb"):
+            P[e.offset:e.offset + e.count] = 1
+    wl = synth.Workload("h", net, [synth.atom(1)], [64], 1.0, 1, 0.1, "fp32", True)
+    fn = make(wl, P)
+    x = synth.init_walkers(wl, 5)
+    out = fn.local_energy(cuda(x))
+    assert fn.sync() == "FN_OK"
+    np.testing.assert_allclose(out["eloc"].cpu().numpy(), -0.5, atol=2e-5)
+    em, g = fn.energy_grad(cuda(x), out["eloc"])
+    assert abs(em.item() + 0.5) < 2e-5
+    assert float(g.abs().max()) < 1e-4
+
+
+def test_empty_batch_and_bad_batch():
+    from paper_2011_07125_gb300.binding import FermiNetError
+    wl, lay, P, x, geo = setup("c4h4x8", 2)
+    fn = make(wl, P)
+    with pytest.raises(FermiNetError):
+        fn.logpsi(cuda(x[:5]))
+    wl1, _, P1, x1, _ = setup("li", 4)
+    fn1 = make(wl1, P1)
+    lp, sg = fn1.logpsi(cuda(x1[:0]))
+    assert lp.numel() == 0
+    assert fn1.sync() == "FN_OK"
+
+
+def test_singular_walker_reported():
+    """Two up electrons at the same point make every up determinant vanish:
+    log|psi| = -inf, sign 0, and the status word reports it."""
+    wl, lay, P, x, geo = setup("li", 4)
+    x = x.copy()
+    x[1, 1] = x[1, 0]
+    fn = make(wl, P)
+    lp, sg = fn.logpsi(cuda(x))
+    st = fn.sync()
+    lp = lp.cpu().numpy()
+    assert st == "FN_ESINGULAR"
+    assert np.isneginf(lp[1]) and sg.cpu().numpy()[1] == 0
+    assert np.all(np.isfinite(lp[[0, 2, 3]]))
