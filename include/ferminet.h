@@ -111,6 +111,32 @@ fn_status ferminet_net_layout(const fn_net* net, fn_param_entry* out, int max_en
  * buffers (and refreshes the BF16 copies of the mixed path).  Stream-ordered. */
 fn_status ferminet_set_params(fn_ctx* ctx, const float* d_params);
 
+/* log|psi| and sign, like ferminet_logpsi, for callers that cannot allocate
+ * device memory: code embedded in a host framework that owns every device
+ * buffer and forbids allocation inside its callbacks, or a process whose device
+ * memory is already fully reserved by another allocator.  The paper has no
+ * counterpart; this is an interface convenience.
+ *
+ * Needs no context: net, d_params (n_params floats, device, in the layout of
+ * ferminet_net_layout), d_R ([n_nuc][3] float32, device, one geometry for all
+ * walkers), d_x ([B][n][3]), d_logpsi ([B]) and d_sign ([B], may be NULL) are
+ * all caller-owned.  The workspace is a fixed 32 MiB device array inside the
+ * library (held by every GPU that loads the library until the process exits);
+ * the call allocates nothing, host or device.  Large batches are processed in
+ * walker chunks that fit the array.  Returns FN_ENOMEM, without launching
+ * anything, when a single walker needs more than the 32 MiB (a very wide or
+ * very large network); FN_EINVAL for bad arguments.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Work is enqueued on `stream` (a cudaStream_t, NULL = default).
+ * All calls share the one array and each call rewrites what it reads, but two
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads on the same device) race on it: serialise them.  Ill-conditioning
+ * and singularity counters are cleared at every call and are not reported. */
+fn_status ferminet_logpsi_noalloc(const fn_net* net, const float* d_params, const float* d_R, const float* d_x,
+                                  long B, float* d_logpsi, float* d_sign, void* stream);
+
 /* log|psi| and sign (Eq. 3) for B walkers.  d_x [B][n][3]; d_logpsi, d_sign [B]
  * (d_sign may be NULL).  A walker whose psi is exactly zero gets -inf and 0. */
 fn_status ferminet_logpsi(fn_ctx* ctx, const float* d_x, long B, float* d_logpsi, float* d_sign);

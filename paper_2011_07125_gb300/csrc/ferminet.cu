@@ -553,6 +553,82 @@ fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* 
 
 }  // namespace
 
+namespace fn {
+
+// Value pass over B walkers of one geometry with a caller-supplied workspace
+// and no allocation of any kind (host or device).  The first 256 bytes of ws
+// hold the status and flag words; the rest is cut into walker chunks.
+fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, const float* d_R, const float* d_x,
+                                     long B, float* d_logpsi, float* d_sign, cudaStream_t s, char* ws,
+                                     size_t ws_size) {
+  fn_ctx c;
+  c.net = net;
+  c.n = net.n_up + net.n_down;
+  c.N = net.n_nuc;
+  c.G = 1;
+  c.Ct = tangent_cols(c.n);
+  c.stream = s;
+  c.ns_max = std::max(net.n_up, net.n_down);
+  // parameter offsets (same order as build_layout, computed without the entry table)
+  long off = 0;
+  for (int l = 0; l < net.n_layers; ++l) {
+    const long a = din1_of(net, l), e = din2_of(net, l);
+    c.lay.V[l] = off;
+    off += (long)net.d1 * (3 * a + 2 * e);
+    c.lay.b[l] = off;
+    off += net.d1;
+    if (l < net.n_layers - 1) {
+      c.lay.W[l] = off;
+      off += (long)net.d2 * e;
+      c.lay.c[l] = off;
+      off += net.d2;
+    }
+  }
+  const long K = net.n_det;
+  c.lay.w_orb = off;
+  off += K * c.n * net.d1;
+  c.lay.g_orb = off;
+  off += K * c.n;
+  c.lay.pi[0] = off;
+  off += K * net.n_up * net.n_nuc;
+  c.lay.pi[1] = off;
+  off += K * net.n_down * net.n_nuc;
+  c.lay.sigma[0] = off;
+  off += K * net.n_up * net.n_nuc;
+  c.lay.sigma[1] = off;
+  off += K * net.n_down * net.n_nuc;
+  c.lay.total = off;
+  c.d_params = const_cast<float*>(d_params);
+  c.d_R = const_cast<float*>(d_R);
+  c.d_status = reinterpret_cast<unsigned*>(ws);
+  c.d_flagged = reinterpret_cast<unsigned long long*>(ws + 64);
+  const size_t head = 256;
+  if (ws_size <= head) return FN_ENOMEM;
+  const size_t avail = ws_size - head;
+  const size_t b1 = ws_bytes(&c, 1, 0), b2 = ws_bytes(&c, 2, 0);
+  if (b1 > avail) return FN_ENOMEM;
+  const size_t per = b2 > b1 ? b2 - b1 : 1, base = b1 > per ? b1 - per : 0;
+  long ch = (long)((avail - base) / per);
+  if (ch < 1) ch = 1;
+  while (ch > 1 && ws_bytes(&c, ch, 0) > avail) --ch;
+  if (ch > B) ch = B;
+  if (cudaMemsetAsync(ws, 0, head, s) != cudaSuccess) return FN_ECUDA;
+  const long n3 = 3L * c.n;
+  for (long w0 = 0; w0 < B; w0 += ch) {
+    const long Bc = std::min(ch, B - w0);
+    Arena ar;
+    ar.measure = false;
+    ar.base = ws + head;
+    FwdOut o;
+    o.logpsi = d_logpsi + w0;
+    o.sign = d_sign ? d_sign + w0 : nullptr;
+    forward(&c, ar, d_x + w0 * n3, Bc, w0, false, false, o, nullptr);
+  }
+  return cudaGetLastError() == cudaSuccess ? FN_OK : FN_ECUDA;
+}
+
+}  // namespace fn
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

@@ -205,3 +205,10 @@ struct fn_ctx {
   long prof_n[FN_KC_COUNT] = {};
   double prof_flops[FN_KC_COUNT] = {};
 };
+
+namespace fn {
+// Value pass with a caller-supplied workspace; allocates nothing (ferminet.cu).
+fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, const float* d_R, const float* d_x,
+                                     long B, float* d_logpsi, float* d_sign, cudaStream_t s, char* ws,
+                                     size_t ws_size);
+}  // namespace fn
