@@ -1,0 +1,29 @@
+/*
+ * ferminet_diag.h — diagnostic entry points of libferminet (not part of the
+ * method's interface; used by the test suite to check kernels in isolation).
+ */
+#ifndef FERMINET_DIAG_H
+#define FERMINET_DIAG_H
+
+#include "ferminet.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The tcgen05 BF16 GEMM that runs the layer contractions of the local-energy
+ * pass (mixed precision), in its plain-store mode:
+ *   C[n][m] = sum_k A[m][k] * B[n][k]   (FP32 accumulation in tensor memory)
+ * d_A: [M][K] bf16, d_B: [N][K] bf16 (both row-major, K a multiple of 64,
+ * 16-byte aligned); d_C: [N][M] float32.  tile_n: rows of B per tile (a multiple
+ * of 16, 16..256).  d_status: a device word; the value 4 is OR-ed into it if a bounded wait
+ * inside the kernel timed out.  Asynchronous on `stream`.  FN_EINVAL for bad
+ * shapes or if the tensor-map encoder is unavailable. */
+fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, float* d_C, int M, int N, int K, int tile_n,
+                                  void* stream, unsigned* d_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FERMINET_DIAG_H */

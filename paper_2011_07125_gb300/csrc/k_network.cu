@@ -170,34 +170,57 @@ __global__ void k_tanh_fl(const float* __restrict__ Z, const float* __restrict__
   for (int c = n3 + 2; c < C; ++c) Hout[base + (long)c * d1] = 0.f;
 }
 
-// Two-electron layer h_ij -> tanh(W h_ij + c) (+ h_ij), one thread per
-// (pair, output feature), all Q rows at once.  The Laplacian rule uses
-// |dz|^2 = 2 |dz/dr_i|^2 because dz/dr_j = -dz/dr_i.
-__global__ void k_two_layer(const float* __restrict__ Ein, long Bc, int n, int Q, int din2, int d2,
-                            const float* __restrict__ W, const float* __restrict__ cb, int residual,
-                            float* __restrict__ Eout, float* __restrict__ Y2) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long tot = Bc * n * n * d2;
-  if (idx >= tot) return;
-  int f = (int)(idx % d2);
-  long p = idx / d2;
-  const float* in = Ein + p * Q * din2;
-  const float* wr = W + (long)f * din2;
-  float z[kQ] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int k = 0; k < din2; ++k) {
-    float wk = wr[k];
-    for (int q = 0; q < Q; ++q) z[q] = fmaf(wk, in[q * din2 + k], z[q]);
+// Two-electron layer h_ij -> tanh(W h_ij + c) (+ h_ij).  One warp per pair at
+// a time (grid-stride over pairs), lane f = output feature, its row of W held
+// in registers; the pair's Q x DIN input rows are staged in shared memory and
+// read as broadcasts.  The Laplacian rule uses |dz|^2 = 2 |dz/dr_i|^2 because
+// dz/dr_j = -dz/dr_i.
+template <int DIN>
+__global__ void __launch_bounds__(256) k_two_layer(const float* __restrict__ Ein, long pairs, int Q, int din2,
+                                                   int d2, const float* __restrict__ W,
+                                                   const float* __restrict__ cb, int residual,
+                                                   float* __restrict__ Eout, float* __restrict__ Y2) {
+  __shared__ __align__(16) float in_s[8][kQ * DIN];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int f = lane;
+  float wr[DIN];
+#pragma unroll
+  for (int k = 0; k < DIN; ++k) wr[k] = (f < d2 && k < din2) ? W[(long)f * din2 + k] : 0.f;
+  const float bias = f < d2 ? cb[f] : 0.f;
+  float* sh = in_s[wib];
+  const long nwarps = (long)gridDim.x * 8;
+  for (long p = (long)blockIdx.x * 8 + wib; p < pairs; p += nwarps) {
+    const float* in = Ein + p * Q * din2;
+    for (int t = lane; t < Q * DIN; t += 32) {
+      const int q = t / DIN, k = t % DIN;
+      sh[t] = k < din2 ? in[q * din2 + k] : 0.f;
+    }
+    __syncwarp();
+    float z[kQ] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < DIN; ++k) {
+      z[0] = fmaf(wr[k], sh[k], z[0]);
+      if (Q > 1) {
+#pragma unroll
+        for (int q = 1; q < kQ; ++q) z[q] = fmaf(wr[k], sh[q * DIN + k], z[q]);
+      }
+    }
+    if (f < d2) {
+      z[0] += bias;
+      const float y = tanhf(z[0]);
+      const float s = 1.f - y * y;
+      if (Y2) Y2[p * d2 + f] = y;
+      float* out = Eout + p * Q * d2;
+      out[f] = y + (residual ? sh[f] : 0.f);
+      if (Q > 1) {
+        const float sq = z[1] * z[1] + z[2] * z[2] + z[3] * z[3];
+#pragma unroll
+        for (int q = 1; q <= 3; ++q) out[q * d2 + f] = s * z[q] + (residual ? sh[q * DIN + f] : 0.f);
+        out[4 * d2 + f] = s * z[4] - 4.f * y * s * sq + (residual ? sh[4 * DIN + f] : 0.f);
+      }
+    }
+    __syncwarp();
   }
-  z[0] += cb[f];
-  float y = tanhf(z[0]);
-  float s = 1.f - y * y;
-  if (Y2) Y2[idx] = y;
-  float* out = Eout + p * Q * d2;
-  out[f] = y + (residual ? in[f] : 0.f);
-  if (Q == 1) return;
-  float sq = z[1] * z[1] + z[2] * z[2] + z[3] * z[3];
-  for (int q = 1; q <= 3; ++q) out[q * d2 + f] = s * z[q] + (residual ? in[q * din2 + f] : 0.f);
-  out[4 * d2 + f] = s * z[4] - 4.f * y * s * sq + (residual ? in[4 * din2 + f] : 0.f);
 }
 
 inline unsigned nblk(long tot, int bs) { return (unsigned)((tot + bs - 1) / bs); }
@@ -230,8 +253,19 @@ void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, 
 
 void launch_two_layer(cudaStream_t s, const float* Ein, long Bc, int n, int Q, int din2, int d2, const float* W,
                       const float* c, bool residual, float* Eout, float* Y2) {
-  long tot = Bc * n * n * d2;
-  if (tot > 0) FN_COUNT(1), k_two_layer<<<nblk(tot, 256), 256, 0, s>>>(Ein, Bc, n, Q, din2, d2, W, c, residual ? 1 : 0, Eout, Y2);
+  const long pairs = Bc * n * n;
+  if (pairs <= 0) return;
+  long blocks = (pairs + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const int r = residual ? 1 : 0;
+  if (din2 <= 4)
+    FN_COUNT(1), k_two_layer<4><<<(unsigned)blocks, 256, 0, s>>>(Ein, pairs, Q, din2, d2, W, c, r, Eout, Y2);
+  else if (din2 <= 8)
+    FN_COUNT(1), k_two_layer<8><<<(unsigned)blocks, 256, 0, s>>>(Ein, pairs, Q, din2, d2, W, c, r, Eout, Y2);
+  else if (din2 <= 16)
+    FN_COUNT(1), k_two_layer<16><<<(unsigned)blocks, 256, 0, s>>>(Ein, pairs, Q, din2, d2, W, c, r, Eout, Y2);
+  else
+    FN_COUNT(1), k_two_layer<32><<<(unsigned)blocks, 256, 0, s>>>(Ein, pairs, Q, din2, d2, W, c, r, Eout, Y2);
 }
 
 }  // namespace fn

@@ -1,0 +1,439 @@
+// BF16 tensor-core GEMM for the local-energy pass (sm_103a: TMA + tcgen05.mma
+// with the accumulator in tensor memory).
+//
+//   D[f][r] = sum_seg sum_k A_seg[f][k] * B_seg[r][k]
+//
+// f runs over output features (the MMA M dimension, 128 per tile) and r over
+// activation rows (walker, electron, tangent column) (the MMA N dimension, up
+// to 256 per tile).  Putting the features on M places one feature per TMEM lane,
+// so the epilogue thread of a lane holds every tangent column of a
+// (walker, electron) group in its own registers: the forward-Laplacian tanh
+// rule (which needs sum_c z_c^2 over the columns of a group) is then a
+// per-thread loop, fused into the GEMM epilogue.
+//
+// Precision: operands are BF16, accumulation FP32 in TMEM.  With terms = 3 each
+// operand is split into hi + lo BF16 parts and the tile accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 significant bits per operand).
+//
+// Structure: persistent CTAs (one per SM, 192 threads): warp 0 issues TMA loads
+// into a 4-stage shared-memory ring, warp 1 (one elected lane) issues
+// tcgen05.mma into one of two TMEM accumulators (2 x 256 columns) and commits to
+// mbarriers, warps 2-5 run the epilogue (tcgen05.ld, one TMEM lane quarter per
+// warp) while the next tile accumulates.  Every wait is bounded: after about a
+// second the waiting role sets an abort flag and the status word, all roles
+// drain, and TMEM is released.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "fn_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace fn {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;            // 64 bf16 = 128 bytes: one swizzle row
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES_MAX = 256 * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES_MAX;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.  Returns false if the
+// kernel is aborting (timeout here or elsewhere).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > TIMEOUT_CYCLES) {
+      *abort_flag = 1;
+      atomicOr(status, (unsigned)ST_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride-dimension byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGemmArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&tfull[s], 1);
+      mbar_init(&tempty[s], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    for (int sg = 0; sg < a.nseg; ++sg)
+      for (int h = 0; h < 2; ++h) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.A[sg][h])) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.B[sg][h])) : "memory");
+      }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int tile_n = a.tile_n;
+  const long total_tiles = (long)a.n_tiles_n * a.n_tiles_m;
+  const uint32_t b_bytes = (uint32_t)tile_n * BK * 2;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const int tn = (int)(tile / a.n_tiles_m), tm = (int)(tile % a.n_tiles_m);
+        bool ok = true;
+        for (int sg = 0; sg < a.nseg && ok; ++sg)
+          for (int kb = 0; kb < a.kblocks[sg] && ok; ++kb)
+            for (int t = 0; t < a.terms && ok; ++t) {
+              if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status)) {
+                ok = false;
+                break;
+              }
+              const int ai = (t == 2) ? 1 : 0, bi = (t == 1) ? 1 : 0;
+              uint8_t* sa = smem + stage * STAGE_BYTES;
+              uint8_t* sb = sa + A_BYTES;
+              mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
+              tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
+              tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
+              if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, tile_n);
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, a.status)) break;
+        fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
+        bool ok = true;
+        uint32_t first = 1;
+        for (int sg = 0; sg < a.nseg && ok; ++sg)
+          for (int kb = 0; kb < a.kblocks[sg] && ok; ++kb)
+            for (int t = 0; t < a.terms && ok; ++t) {
+              if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
+                ok = false;
+                break;
+              }
+              fence_after();
+              const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+              const uint32_t sb = sa + A_BYTES;
+              const uint64_t da = smem_desc(sa), db = smem_desc(sb);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                // 16 bf16 = 32 bytes along K inside the swizzle row: +2 in the address field
+                mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, first ? 0u : 1u);
+                first = 0;
+              }
+              mma_commit(&empty[stage]);
+              if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    const int lane_base = quarter * 32;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      const int tn = (int)(tile / a.n_tiles_m), tm = (int)(tile % a.n_tiles_m);
+      if (!mbar_wait(&tfull[acc], acc_phase, abort_flag, a.status)) break;
+      fence_after();
+      const int f = tm * BM + lane_base + lane;
+      const bool fok = f < a.mfeat;
+      const uint32_t tbase = tmem_base + ((uint32_t)lane_base << 16) + (uint32_t)(acc * 256);
+      const long r_tile = (long)tn * tile_n;
+      if (a.mode == 0) {
+        for (int c0 = 0; c0 < tile_n; c0 += 8) {
+          float v[8];
+          tmem_ld8(tbase + c0, v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long r = r_tile + c0 + j;
+            if (fok && r < a.rows) {
+              float z = v[j];
+              if (a.bias && (r % a.bias_period) == 0) z += a.bias[f];
+              a.out[r * a.ldo + f] = z;
+            }
+          }
+        }
+      } else {
+        const int C = a.C, n3 = a.n3;
+        const int groups = tile_n / C;
+        const float bf = (fok && a.bias) ? a.bias[f] : 0.f;
+        for (int gi = 0; gi < groups; ++gi) {
+          const long r0 = r_tile + (long)gi * C;
+          const bool gok = fok && r0 < a.rows;
+          const long urow = (r0 / a.u_div) * C;
+          // pass 1: value column and sum of squared tangents
+          float z0 = 0.f, sq = 0.f;
+          for (int c0 = 0; c0 < C; c0 += 8) {
+            float v[8];
+            tmem_ld8(tbase + gi * C + c0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int c = c0 + j;
+              float z = v[j];
+              if (gok) z += a.U[(urow + c) * a.ldu + f];
+              if (c == 0) z0 = z + bf;
+              else if (c <= n3) sq = fmaf(z, z, sq);
+            }
+          }
+          const float y = tanhf(z0);
+          const float s = 1.f - y * y;
+          // pass 2: outputs
+          for (int c0 = 0; c0 < C; c0 += 8) {
+            float v[8];
+            tmem_ld8(tbase + gi * C + c0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int c = c0 + j;
+              if (!gok) continue;
+              const long r = r0 + c;
+              const float z = v[j] + a.U[(urow + c) * a.ldu + f];
+              float o;
+              if (c == 0) o = y;
+              else if (c <= n3) o = s * z;
+              else if (c == n3 + 1) o = s * z - 2.f * y * s * sq;
+              else o = 0.f;
+              if (a.res) o += a.res[r * a.ldh + f];
+              a.h_out[r * a.ldh + f] = o;
+              const __nv_bfloat16 hi = __float2bfloat16_rn(o);
+              a.hb_hi[r * a.ldhb + f] = hi;
+              if (a.hb_lo) a.hb_lo[r * a.ldhb + f] = __float2bfloat16_rn(o - __bfloat162float(hi));
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+}  // namespace
+
+bool tc_encode_ready() {
+  std::call_once(g_encode_once, [] {
+    void* fnp = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fnp, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fnp);
+    else
+      cudaGetLastError();
+  });
+  return g_encode != nullptr;
+}
+
+bool tc_make_map(CUtensorMap* tm, const void* base, long rows, long ld_elems, int box_rows) {
+  if (!tc_encode_ready()) return false;
+  if (((uintptr_t)base & 15) || (ld_elems % BK) || rows < 1 || box_rows < 1 || box_rows > 256) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld_elems, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_elems * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int tc_num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.terms < 1 || a.terms > 3 || a.nseg < 1 ||
+      a.nseg > 2)
+    return FN_EINVAL;
+  const long total = (long)a.n_tiles_n * a.n_tiles_m;
+  if (total <= 0) return FN_OK;
+  int grid = tc_num_sms();
+  if (total < grid) grid = (int)total;
+  FN_COUNT(1), k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(a);
+  return FN_OK;
+}
+
+}  // namespace fn
+
+extern "C" fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, float* d_C, int M, int N, int K,
+                                             int tile_n, void* stream, unsigned* d_status) {
+  using namespace fn;
+  if (!d_A || !d_B || !d_C || !d_status || M < 1 || N < 1 || K < 1 || K % BK) return FN_EINVAL;
+  TcGemmArgs a{};
+  if (!tc_make_map(&a.A[0][0], d_A, M, K, BM) || !tc_make_map(&a.B[0][0], d_B, N, K, tile_n)) return FN_EINVAL;
+  a.A[0][1] = a.A[0][0];
+  a.B[0][1] = a.B[0][0];
+  a.kblocks[0] = K / BK;
+  a.nseg = 1;
+  a.terms = 1;
+  a.rows = N;
+  a.mfeat = M;
+  a.tile_n = tile_n;
+  a.n_tiles_n = (N + tile_n - 1) / tile_n;
+  a.n_tiles_m = (M + BM - 1) / BM;
+  a.mode = 0;
+  a.out = d_C;
+  a.ldo = M;
+  a.bias_period = 1;
+  a.status = d_status;
+  return tc_gemm_launch((cudaStream_t)stream, a);
+}

@@ -12,8 +12,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "ferminet.h")).read()
-    return sorted(set(re.findall(r"\b(ferminet_\w+)\s*\(", src)))
+    names = set()
+    for h in ("ferminet.h", "ferminet_diag.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        names |= set(re.findall(r"\b(ferminet_\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_symbols_exported():
