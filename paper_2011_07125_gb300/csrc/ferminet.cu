@@ -17,6 +17,7 @@
 #include <cstring>
 
 #include "fn_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace fn {
 
@@ -171,6 +172,34 @@ void drain_profile(fn_ctx* c) {
 
 Geo geo_of(fn_ctx* c) { return Geo{c->d_R, c->d_Z, c->d_Enn64, c->G > 1 ? c->d_geo : nullptr}; }
 
+inline long pad64(long v) { return ((v + 63) / 64) * 64; }
+
+// Rows per tile of the fused layer epilogue: whole (walker, electron) groups of
+// C columns, at most 256 rows, a multiple of 16.
+int layer_tile(int C) {
+  for (int g = 256 / C; g >= 1; --g)
+    if ((g * C) % 16 == 0) return g * C;
+  return 0;
+}
+
+int plain_tile(long rows) { return rows >= 256 ? 256 : (int)(((rows + 15) / 16) * 16); }
+
+// Tensor maps of one GEMM segment: weights (hi, lo) [mfeat][ldw] and
+// activations (hi, lo) [rows][lda].
+bool tc_segment(TcGemmArgs& g, int seg, const __nv_bfloat16* w_hi, const __nv_bfloat16* w_lo, long mfeat, long ldw,
+                const __nv_bfloat16* x_hi, const __nv_bfloat16* x_lo, long rows, long lda, int tile_n) {
+  if (ldw != lda) return false;
+  bool ok = tc_make_map(&g.A[seg][0], w_hi, mfeat, ldw, 128) && tc_make_map(&g.B[seg][0], x_hi, rows, lda, tile_n);
+  if (w_lo && x_lo)
+    ok = ok && tc_make_map(&g.A[seg][1], w_lo, mfeat, ldw, 128) && tc_make_map(&g.B[seg][1], x_lo, rows, lda, tile_n);
+  else {
+    g.A[seg][1] = g.A[seg][0];
+    g.B[seg][1] = g.B[seg][0];
+  }
+  g.kblocks[seg] = (int)(lda / 64);
+  return ok;
+}
+
 // One network pass (see the file comment) over walkers [w0, w0 + Bc).
 void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangent, bool store, const FwdOut& out,
              Stored* st) {
@@ -199,8 +228,10 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
       }
     }
   } else {
-    Ha = ar.get<float>(rows * d1);
-    Hb = ar.get<float>(rows * d1);
+    if (!(c->prec == FN_PREC_MIXED && c->tc_ok && layer_tile(C) > 0)) {
+      Ha = ar.get<float>(rows * d1);
+      Hb = ar.get<float>(rows * d1);
+    }
     if (L > 1) {
       Ea = ar.get<float>(pairs * Q * d2);
       Eb = ar.get<float>(pairs * Q * d2);
@@ -209,7 +240,20 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     M2 = ar.get<float>(rows * 2 * max_din2);
   }
   float* U = ar.get<float>(Bc * C * d1);
-  float* Z = ar.get<float>(rows * d1);
+  const bool tc = !store && c->prec == FN_PREC_MIXED && c->tc_ok && layer_tile(C) > 0;
+  const bool two = c->terms > 1;
+  float* Z = tc ? nullptr : ar.get<float>(rows * d1);
+  __nv_bfloat16 *H0b[2] = {}, *Hab[2] = {}, *Hbb[2] = {}, *M1b[2] = {}, *M2b[2] = {};
+  const long ldh0 = pad64(4 * N), ldh = pad64(d1), ldm1 = pad64(2 * max_din1), ldm2 = pad64(2 * max_din2);
+  if (tc) {
+    for (int h = 0; h < (two ? 2 : 1); ++h) {
+      H0b[h] = ar.get<__nv_bfloat16>(rows * ldh0);
+      Hab[h] = ar.get<__nv_bfloat16>(rows * ldh);
+      Hbb[h] = ar.get<__nv_bfloat16>(rows * ldh);
+      M1b[h] = ar.get<__nv_bfloat16>(Bc * C * ldm1);
+      M2b[h] = ar.get<__nv_bfloat16>(rows * ldm2);
+    }
+  }
   float* O = ar.get<float>(rows * Ktot);
   float* logdet = ar.get<float>(Bc * K * 2);
   float* sgn = ar.get<float>(Bc * K * 2);
@@ -230,7 +274,118 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   launch_features(s, x, Bc, w0, n, N, C, Q, g, H0, E0);
   const float* Hc = H0;
   const float* Ec = E0;
-  for (int l = 0; l < L; ++l) {
+  if (tc) {
+    // Local-energy pass on the tensor cores: BF16 operands (hi, or hi + lo),
+    // FP32 accumulation, fused forward-Laplacian tanh epilogue.
+    const double fl_rows = 2.0 * (double)Bc * Creal;
+    launch_split_bf16(s, H0, 4 * N, rows, 4 * N, H0b[0], H0b[1], ldh0);
+    const __nv_bfloat16* Hcb[2] = {H0b[0], H0b[1]};
+    long ldc_b = ldh0;
+    const int tl = tangent ? layer_tile(C) : plain_tile(rows);
+    if (ldh != d1) {
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        cudaMemsetAsync(Hab[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
+        cudaMemsetAsync(Hbb[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
+      }
+    }
+    for (int l = 0; l < L; ++l) {
+      const int a1 = din1_of(t, l), a2 = din2_of(t, l);
+      const long l1 = pad64(2 * a1), l2 = pad64(2 * a2);
+      {
+        Prof pm(c, tangent ? FN_KC_MEANS : FN_KC_COUNT, 0.0);
+        if (l == 0) {
+          launch_mean1(s, H0, Bc, n, t.n_up, C, a1, M1);
+          launch_split_bf16(s, M1, 2 * a1, Bc * C, 2 * a1, M1b[0], M1b[1], l1);
+        } else {
+          launch_mean1_bf16(s, Hcb[0], Hcb[1], ldc_b, Bc, n, t.n_up, C, a1, M1b[0], M1b[1], l1);
+        }
+        launch_mean2_bf16(s, Ec, Bc, n, t.n_up, Q, a2, C, M2b[0], M2b[1], l2);
+      }
+      {
+        Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * d1 * 2.0 * a1);
+        TcGemmArgs u{};
+        const int tu = plain_tile(Bc * C);
+        bool ok = tc_segment(u, 0, c->wb_hi + c->wb_bc[l], two ? c->wb_lo + c->wb_bc[l] : nullptr, d1, c->ld_bc[l],
+                             M1b[0], M1b[1], Bc * C, l1, tu);
+        u.nseg = 1;
+        u.terms = c->terms;
+        u.rows = Bc * C;
+        u.mfeat = d1;
+        u.tile_n = tu;
+        u.n_tiles_n = (int)((Bc * C + tu - 1) / tu);
+        u.n_tiles_m = (d1 + 127) / 128;
+        u.mode = 0;
+        u.out = U;
+        u.ldo = d1;
+        u.bias_period = 1;
+        u.status = c->d_status;
+        if (!ok || tc_gemm_launch(s, u) != FN_OK) c->host_fail = true;
+      }
+      __nv_bfloat16** Hnb = (l % 2 == 0) ? Hab : Hbb;
+      {
+        Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * n * d1 * (double)(a1 + 2 * a2));
+        TcGemmArgs m{};
+        bool ok = tc_segment(m, 0, c->wb_hi + c->wb_a[l], two ? c->wb_lo + c->wb_a[l] : nullptr, d1, c->ld_a[l],
+                             Hcb[0], Hcb[1], rows, ldc_b, tl);
+        ok = ok && tc_segment(m, 1, c->wb_hi + c->wb_de[l], two ? c->wb_lo + c->wb_de[l] : nullptr, d1,
+                              c->ld_de[l], M2b[0], M2b[1], rows, l2, tl);
+        m.nseg = 2;
+        m.terms = c->terms;
+        m.rows = rows;
+        m.mfeat = d1;
+        m.tile_n = tl;
+        m.n_tiles_n = (int)((rows + tl - 1) / tl);
+        m.n_tiles_m = (d1 + 127) / 128;
+        m.mode = tangent ? 1 : 2;
+        m.bias = P + c->lay.b[l];
+        m.bias_period = C;
+        m.C = C;
+        m.n3 = 3 * n;
+        m.U = U;
+        m.u_div = (long)n * C;
+        m.ldu = d1;
+        m.res_hi = l >= 1 ? Hcb[0] : nullptr;
+        m.res_lo = (l >= 1 && two) ? Hcb[1] : nullptr;
+        m.hb_hi = Hnb[0];
+        m.hb_lo = two ? Hnb[1] : nullptr;
+        m.ldhb = ldh;
+        m.status = c->d_status;
+        if (!ok || tc_gemm_launch(s, m) != FN_OK) c->host_fail = true;
+      }
+      if (l < L - 1) {
+        float* En = (l % 2 == 0) ? Ea : Eb;
+        Prof p2(c, FN_KC_TWO_LAYER, 2.0 * (double)pairs * Q * d2 * a2);
+        launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En, nullptr);
+        Ec = En;
+      }
+      Hcb[0] = Hnb[0];
+      Hcb[1] = Hnb[1];
+      ldc_b = ldh;
+    }
+    {
+      const double same_spin = (double)t.n_up * t.n_up + (double)t.n_down * t.n_down;
+      Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, 2.0 * (double)Bc * Creal * d1 * K * same_spin);
+      TcGemmArgs o{};
+      const int to = plain_tile(rows);
+      bool ok = tc_segment(o, 0, c->wb_hi + c->wb_orb, two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb,
+                           Hcb[0], Hcb[1], rows, ldh, to);
+      o.nseg = 1;
+      o.terms = c->terms;
+      o.rows = rows;
+      o.mfeat = (int)Ktot;
+      o.tile_n = to;
+      o.n_tiles_n = (int)((rows + to - 1) / to);
+      o.n_tiles_m = (int)((Ktot + 127) / 128);
+      o.mode = 0;
+      o.out = O;
+      o.ldo = Ktot;
+      o.bias = P + c->lay.g_orb;
+      o.bias_period = C;
+      o.status = c->d_status;
+      if (!ok || tc_gemm_launch(s, o) != FN_OK) c->host_fail = true;
+    }
+  }
+  for (int l = 0; l < L && !tc; ++l) {
     const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
     const float* V = P + c->lay.V[l];
     float* M1l = store ? st->M1[l] : M1;
@@ -279,7 +434,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   Epi eo;
   eo.bias = P + c->lay.g_orb;
   eo.bias_period = C;
-  {
+  if (!tc) {
     const double same_spin = (double)t.n_up * t.n_up + (double)t.n_down * t.n_down;
     Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, 2.0 * (double)Bc * Creal * d1 * K * same_spin);
     gemm_nt(s, rows, Ktot, d1, Hc, d1, P + c->lay.w_orb, d1, O, Ktot, eo);
@@ -526,6 +681,10 @@ fn_status run_passes(fn_ctx* c, const float* x, long B, bool tangent, const FwdO
     o.kinetic = out.kinetic ? out.kinetic + w0 : nullptr;
     Prof pv(c, tangent ? FN_KC_COUNT : FN_KC_VALUE_PASS, 0.0);
     forward(c, ar, x + w0 * n3, Bc, w0, tangent, false, o, nullptr);
+    if (c->host_fail) {
+      c->host_fail = false;
+      return fail(c, FN_ECUDA, "tensor-core GEMM set-up failed (tensor map or launch)");
+    }
   }
   return after_launch(c);
 }
@@ -725,6 +884,32 @@ fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms
   if (bad(cudaMemcpy(c->d_geo_cnt, cnt.data(), sizeof(long) * n_geoms, cudaMemcpyHostToDevice))) return FN_ECUDA;
   if (bad(cudaMemset(c->d_status, 0, sizeof(unsigned)))) return FN_ECUDA;
   if (bad(cudaMemset(c->d_flagged, 0, sizeof(unsigned long long)))) return FN_ECUDA;
+  if (prec == FN_PREC_MIXED) {
+    c->terms = 3;
+    if (const char* v = getenv("FERMINET_MIXED_TERMS")) c->terms = atoi(v) == 1 ? 1 : 3;
+    long off = 0;
+    for (int l = 0; l < t.n_layers; ++l) {
+      const int a1 = din1_of(t, l), a2 = din2_of(t, l);
+      c->ld_a[l] = pad64(a1);
+      c->ld_bc[l] = pad64(2 * a1);
+      c->ld_de[l] = pad64(2 * a2);
+      c->wb_a[l] = off;
+      off += (long)t.d1 * c->ld_a[l];
+      c->wb_bc[l] = off;
+      off += (long)t.d1 * c->ld_bc[l];
+      c->wb_de[l] = off;
+      off += (long)t.d1 * c->ld_de[l];
+    }
+    c->ld_orb = pad64(t.d1);
+    c->wb_orb = off;
+    off += (long)t.n_det * c->n * c->ld_orb;
+    c->wb_total = off;
+    if (bad(cudaMalloc(&c->wb_hi, sizeof(__nv_bfloat16) * off))) return FN_ENOMEM;
+    if (bad(cudaMalloc(&c->wb_lo, sizeof(__nv_bfloat16) * off))) return FN_ENOMEM;
+    if (bad(cudaMemset(c->wb_hi, 0, sizeof(__nv_bfloat16) * off))) return FN_ECUDA;
+    if (bad(cudaMemset(c->wb_lo, 0, sizeof(__nv_bfloat16) * off))) return FN_ECUDA;
+    c->tc_ok = tc_encode_ready();
+  }
   *out = c;
   return FN_OK;
 }
@@ -759,6 +944,22 @@ fn_status ferminet_set_params(fn_ctx* c, const float* d_params) {
   if (!c) return FN_EINVAL;
   if (!d_params) return fail(c, FN_EINVAL, "null parameter pointer");
   CK(cudaMemcpyAsync(c->d_params, d_params, sizeof(float) * c->lay.total, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->prec == FN_PREC_MIXED && c->wb_hi) {
+    const fn_net& t = c->net;
+    const float* P = c->d_params;
+    for (int l = 0; l < t.n_layers; ++l) {
+      const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
+      const float* V = P + c->lay.V[l];
+      launch_split_bf16(c->stream, V, wV, t.d1, a1, c->wb_hi + c->wb_a[l], c->wb_lo + c->wb_a[l], c->ld_a[l]);
+      launch_split_bf16(c->stream, V + a1, wV, t.d1, 2 * a1, c->wb_hi + c->wb_bc[l], c->wb_lo + c->wb_bc[l],
+                        c->ld_bc[l]);
+      launch_split_bf16(c->stream, V + 3 * a1, wV, t.d1, 2 * a2, c->wb_hi + c->wb_de[l], c->wb_lo + c->wb_de[l],
+                        c->ld_de[l]);
+    }
+    launch_split_bf16(c->stream, P + c->lay.w_orb, t.d1, (long)t.n_det * c->n, t.d1, c->wb_hi + c->wb_orb,
+                      c->wb_lo + c->wb_orb, c->ld_orb);
+    CK(cudaGetLastError());
+  }
   c->err.clear();
   return FN_OK;
 }
@@ -888,6 +1089,8 @@ void ferminet_destroy(fn_ctx* c) {
   cudaFree(c->d_flagged);
   cudaFree(c->ws);
   cudaFree(c->aux);
+  cudaFree(c->wb_hi);
+  cudaFree(c->wb_lo);
   drain_profile(c);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;

@@ -1,6 +1,7 @@
 // Library-internal declarations shared by the translation units of libferminet.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -81,6 +82,16 @@ void launch_features(cudaStream_t s, const float* x, long Bc, long w0, int n, in
                      float* H0, float* E0);
 void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int C, int din, float* M1);
 void launch_mean2(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C, float* M2);
+// Same means written as BF16 hi / lo parts (lo may be null) with row stride ldb
+// (>= 2 din2, padding columns zeroed).
+void launch_mean2_bf16(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C,
+                       __nv_bfloat16* hi, __nv_bfloat16* lo, long ldb);
+// Spin means of a BF16 hi + lo activation, written as BF16 hi + lo (padded).
+void launch_mean1_bf16(cudaStream_t s, const __nv_bfloat16* hi, const __nv_bfloat16* lo, long ldin, long Bc, int n,
+                       int n_up, int C, int din, __nv_bfloat16* ohi, __nv_bfloat16* olo, long ldout);
+// dst_hi/lo[r][c] = split of src[r * src_ld + c] for c < cols, 0 for cols <= c < dst_ld.
+void launch_split_bf16(cudaStream_t s, const float* src, long src_ld, long rows, long cols, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, long dst_ld);
 void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, int n, int C, int d1, float* Hout,
                     float* Y);
 void launch_two_layer(cudaStream_t s, const float* Ein, long Bc, int n, int Q, int din2, int d2, const float* W,
@@ -191,6 +202,15 @@ struct fn_ctx {
   int device = 0;
   int ns_max = 0;
   float pivot_tau = 1e-4f;  // FP32 pivot-ratio threshold of the FP64 redo
+  // mixed precision: BF16 hi/lo copies of the layer weights, padded to 64 columns
+  bool tc_ok = false;
+  bool host_fail = false;  // set when a tensor-core launch could not be prepared
+  int terms = 3;
+  __nv_bfloat16* wb_hi = nullptr;
+  __nv_bfloat16* wb_lo = nullptr;
+  long wb_a[16] = {}, wb_bc[16] = {}, wb_de[16] = {}, wb_orb = 0;
+  long ld_a[16] = {}, ld_bc[16] = {}, ld_de[16] = {}, ld_orb = 0;
+  long wb_total = 0;
   int force64 = 0;
   // per-class event timing
   bool prof_on = false;

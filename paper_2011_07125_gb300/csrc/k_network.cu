@@ -143,6 +143,92 @@ __global__ void k_mean2(const float* __restrict__ E, long Bc, int n, int n_up, i
   M2[idx] = out;
 }
 
+// Dense-column spin means of the two-electron stream (see k_mean2), written
+// as BF16 hi / lo parts for the tensor-core GEMM; padding columns are zeroed.
+__global__ void k_mean2_bf16(const float* __restrict__ E, long Bc, int n, int n_up, int Q, int din2, int C,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long ldb) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = Bc * n * C * ldb;
+  if (idx >= tot) return;
+  const int col = (int)(idx % ldb);
+  long r = idx / ldb;
+  float out = 0.f;
+  if (col < 2 * din2) {
+    const int s = col / din2, f = col % din2;
+    const int c = (int)(r % C);
+    const long wi = r / C;
+    const int i = (int)(wi % n);
+    const long w = wi / n;
+    const int j0 = s == 0 ? 0 : n_up, j1 = s == 0 ? n_up : n;
+    const int ns = j1 - j0;
+    if (ns > 0) {
+      const float* Ei = E + (w * n + i) * (long)n * Q * din2;
+      const float inv = 1.f / (float)ns;
+      const int n3 = 3 * n;
+      if (c == 0) {
+        float a = 0.f;
+        for (int j = j0; j < j1; ++j) a += Ei[(long)j * Q * din2 + f];
+        out = a * inv;
+      } else if (Q > 1 && c <= n3) {
+        const int e = (c - 1) / 3, dd = (c - 1) % 3;
+        if (e == i) {
+          float a = 0.f;
+          for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 1 + dd) * din2 + f];
+          out = a * inv;
+        } else if (e >= j0 && e < j1) {
+          out = -Ei[((long)e * Q + 1 + dd) * din2 + f] * inv;
+        }
+      } else if (Q > 1 && c == n3 + 1) {
+        float a = 0.f;
+        for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 4) * din2 + f];
+        out = a * inv;
+      }
+    }
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(out);
+  hi[idx] = h;
+  if (lo) lo[idx] = __float2bfloat16_rn(out - __bfloat162float(h));
+}
+
+// Spin means of a one-electron activation held as BF16 hi + lo (row stride
+// ldin), written as BF16 hi + lo with row stride ldout (padding zeroed):
+// out[w][c][s*din + f] = mean over electrons i of spin s of (hi + lo)[w][i][c][f].
+__global__ void k_mean1_bf16(const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo, long ldin,
+                             long Bc, int n, int n_up, int C, int din, __nv_bfloat16* __restrict__ ohi,
+                             __nv_bfloat16* __restrict__ olo, long ldout) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Bc * C * ldout) return;
+  const int col = (int)(idx % ldout);
+  const long wc = idx / ldout;
+  const int c = (int)(wc % C);
+  const long w = wc / C;
+  float out = 0.f;
+  if (col < 2 * din) {
+    const int s = col / din, f = col % din;
+    const int i0 = s == 0 ? 0 : n_up, i1 = s == 0 ? n_up : n;
+    float acc = 0.f;
+    for (int i = i0; i < i1; ++i) {
+      const long r = ((w * n + i) * C + c) * ldin + f;
+      acc += __bfloat162float(hi[r]) + (lo ? __bfloat162float(lo[r]) : 0.f);
+    }
+    out = i1 > i0 ? acc / (float)(i1 - i0) : 0.f;
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(out);
+  ohi[idx] = h;
+  if (olo) olo[idx] = __float2bfloat16_rn(out - __bfloat162float(h));
+}
+
+__global__ void k_split_bf16(const float* __restrict__ src, long src_ld, long rows, long cols,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long dst_ld) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * dst_ld) return;
+  const long r = idx / dst_ld, c = idx % dst_ld;
+  const float v = c < cols ? src[r * src_ld + c] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[idx] = h;
+  if (lo) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 // One-electron tanh with forward-Laplacian columns, plus residual.
 __global__ void k_tanh_fl(const float* __restrict__ Z, const float* __restrict__ Hres, long Bc, int n, int C,
                           int d1, float* __restrict__ Hout, float* __restrict__ Y) {
@@ -243,6 +329,25 @@ void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int 
 void launch_mean2(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C, float* M2) {
   long tot = Bc * n * C * 2 * din2;
   if (tot > 0) FN_COUNT(1), k_mean2<<<nblk(tot, 256), 256, 0, s>>>(E, Bc, n, n_up, Q, din2, C, M2);
+}
+
+void launch_mean2_bf16(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C,
+                       __nv_bfloat16* hi, __nv_bfloat16* lo, long ldb) {
+  long tot = Bc * n * C * ldb;
+  if (tot > 0) FN_COUNT(1), k_mean2_bf16<<<nblk(tot, 256), 256, 0, s>>>(E, Bc, n, n_up, Q, din2, C, hi, lo, ldb);
+}
+
+void launch_mean1_bf16(cudaStream_t s, const __nv_bfloat16* hi, const __nv_bfloat16* lo, long ldin, long Bc, int n,
+                       int n_up, int C, int din, __nv_bfloat16* ohi, __nv_bfloat16* olo, long ldout) {
+  long tot = Bc * C * ldout;
+  if (tot > 0)
+    FN_COUNT(1), k_mean1_bf16<<<nblk(tot, 256), 256, 0, s>>>(hi, lo, ldin, Bc, n, n_up, C, din, ohi, olo, ldout);
+}
+
+void launch_split_bf16(cudaStream_t s, const float* src, long src_ld, long rows, long cols, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, long dst_ld) {
+  long tot = rows * dst_ld;
+  if (tot > 0) FN_COUNT(1), k_split_bf16<<<nblk(tot, 256), 256, 0, s>>>(src, src_ld, rows, cols, hi, lo, dst_ld);
 }
 
 void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, int n, int C, int d1, float* Hout,

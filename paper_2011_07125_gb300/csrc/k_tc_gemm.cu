@@ -15,11 +15,11 @@
 // operand is split into hi + lo BF16 parts and the tile accumulates
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 significant bits per operand).
 //
-// Structure: persistent CTAs (one per SM, 192 threads): warp 0 issues TMA loads
+// Structure: persistent CTAs (one per SM, 320 threads): warp 0 issues TMA loads
 // into a 4-stage shared-memory ring, warp 1 (one elected lane) issues
 // tcgen05.mma into one of two TMEM accumulators (2 x 256 columns) and commits to
-// mbarriers, warps 2-5 run the epilogue (tcgen05.ld, one TMEM lane quarter per
-// warp) while the next tile accumulates.  Every wait is bounded: after about a
+// mbarriers, warps 2-9 run the epilogue (tcgen05.ld; two warps per TMEM lane
+// quarter, splitting the tile's columns) while the next tile accumulates.  Every wait is bounded: after about a
 // second the waiting role sets an abort flag and the status word, all roles
 // drain, and TMEM is released.
 #include <cuda.h>
@@ -42,6 +42,8 @@ constexpr int B_BYTES_MAX = 256 * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES_MAX;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = (2 + EPI_WARPS) * 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -143,7 +145,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGemmArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ TcGemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&tfull[s], 1);
-      mbar_init(&tempty[s], 4);
+      mbar_init(&tempty[s], EPI_WARPS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,9 +263,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    // epilogue warps 2..9: TMEM lane quarter = warp % 4; the two warps of a
+    // quarter split the tile's column chunks (plain) or groups (layer)
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int lane_base = quarter * 32;
+    const float* __restrict__ Up = a.U;
+    const float* __restrict__ bias = a.bias;
+    const __nv_bfloat16* __restrict__ rh = a.res_hi;
+    const __nv_bfloat16* __restrict__ rl = a.res_lo;
+    __nv_bfloat16* __restrict__ oh = a.hb_hi;
+    __nv_bfloat16* __restrict__ ol = a.hb_lo;
+    float* __restrict__ out = a.out;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
@@ -274,64 +285,105 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcGe
       const bool fok = f < a.mfeat;
       const uint32_t tbase = tmem_base + ((uint32_t)lane_base << 16) + (uint32_t)(acc * 256);
       const long r_tile = (long)tn * tile_n;
-      if (a.mode == 0) {
-        for (int c0 = 0; c0 < tile_n; c0 += 8) {
+      if (a.mode == 2) {
+        // value pass: h = tanh(acc + U[walker] + b) (+ residual), one column per row
+        const float bf = (fok && bias) ? bias[f] : 0.f;
+        const int ldb = (int)a.ldhb;
+        for (int c0 = half * 8; c0 < tile_n; c0 += 16) {
+          const long rr = r_tile + c0;
+          if (rr >= a.rows) break;  // warp-uniform
+          float u8[8], r8[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long r = rr + j;
+            const bool ok = fok && r < a.rows;
+            u8[j] = ok ? Up[(r / a.u_div) * a.ldu + f] : 0.f;
+            r8[j] = (ok && rh) ? __bfloat162float(rh[r * ldb + f]) : 0.f;
+            if (ok && rl) r8[j] += __bfloat162float(rl[r * ldb + f]);
+          }
+          float v[8];
+          tmem_ld8(tbase + c0, v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long r = rr + j;
+            if (!(fok && r < a.rows)) continue;
+            const float o = tanhf(v[j] + u8[j] + bf) + r8[j];
+            const __nv_bfloat16 h = __float2bfloat16_rn(o);
+            oh[r * ldb + f] = h;
+            if (ol) ol[r * ldb + f] = __float2bfloat16_rn(o - __bfloat162float(h));
+          }
+        }
+      } else if (a.mode == 0) {
+        const float bf = (fok && bias) ? bias[f] : 0.f;
+        for (int c0 = half * 8; c0 < tile_n; c0 += 16) {
           float v[8];
           tmem_ld8(tbase + c0, v);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const long r = r_tile + c0 + j;
-            if (fok && r < a.rows) {
-              float z = v[j];
-              if (a.bias && (r % a.bias_period) == 0) z += a.bias[f];
-              a.out[r * a.ldo + f] = z;
-            }
+            if (fok && r < a.rows) out[r * a.ldo + f] = v[j] + ((r % a.bias_period) == 0 ? bf : 0.f);
           }
         }
       } else {
         const int C = a.C, n3 = a.n3;
         const int groups = tile_n / C;
-        const float bf = (fok && a.bias) ? a.bias[f] : 0.f;
-        for (int gi = 0; gi < groups; ++gi) {
+        const float bf = (fok && bias) ? bias[f] : 0.f;
+        const int ldu = (int)a.ldu, ldb = (int)a.ldhb;
+        for (int gi = half; gi < groups; gi += 2) {
           const long r0 = r_tile + (long)gi * C;
-          const bool gok = fok && r0 < a.rows;
-          const long urow = (r0 / a.u_div) * C;
+          if (r0 >= a.rows) continue;  // warp-uniform: no TMEM access for groups past the end
+          const bool gok = fok;       // per lane: loads and stores only
+          // per-group base pointers; column offsets below fit in 32 bits
+          const float* __restrict__ ug = Up + ((r0 / a.u_div) * C) * (long)ldu + (fok ? f : 0);
+          const long rb = r0 * (long)ldb + (fok ? f : 0);
           // pass 1: value column and sum of squared tangents
           float z0 = 0.f, sq = 0.f;
           for (int c0 = 0; c0 < C; c0 += 8) {
+            float u8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) u8[j] = gok ? ug[(c0 + j) * ldu] : 0.f;
             float v[8];
             tmem_ld8(tbase + gi * C + c0, v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int c = c0 + j;
-              float z = v[j];
-              if (gok) z += a.U[(urow + c) * a.ldu + f];
-              if (c == 0) z0 = z + bf;
-              else if (c <= n3) sq = fmaf(z, z, sq);
+              const float z = v[j] + u8[j];
+              z0 = (c == 0) ? z + bf : z0;
+              sq = (c >= 1 && c <= n3) ? fmaf(z, z, sq) : sq;
             }
           }
           const float y = tanhf(z0);
           const float s = 1.f - y * y;
-          // pass 2: outputs
+          const float lapc = -2.f * y * s * sq;
+          const __nv_bfloat16* __restrict__ rhg = rh ? rh + rb : nullptr;
+          const __nv_bfloat16* __restrict__ rlg = rl ? rl + rb : nullptr;
+          __nv_bfloat16* __restrict__ ohg = oh + rb;
+          __nv_bfloat16* __restrict__ olg = ol ? ol + rb : nullptr;
+          // pass 2: outputs (+ residual), stored as BF16 hi + lo
           for (int c0 = 0; c0 < C; c0 += 8) {
+            float u8[8], r8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int off = (c0 + j) * ldb;
+              u8[j] = gok ? ug[(c0 + j) * ldu] : 0.f;
+              r8[j] = (gok && rhg) ? __bfloat162float(rhg[off]) : 0.f;
+              if (gok && rlg) r8[j] += __bfloat162float(rlg[off]);
+            }
             float v[8];
             tmem_ld8(tbase + gi * C + c0, v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int c = c0 + j;
-              if (!gok) continue;
-              const long r = r0 + c;
-              const float z = v[j] + a.U[(urow + c) * a.ldu + f];
-              float o;
-              if (c == 0) o = y;
-              else if (c <= n3) o = s * z;
-              else if (c == n3 + 1) o = s * z - 2.f * y * s * sq;
-              else o = 0.f;
-              if (a.res) o += a.res[r * a.ldh + f];
-              a.h_out[r * a.ldh + f] = o;
-              const __nv_bfloat16 hi = __float2bfloat16_rn(o);
-              a.hb_hi[r * a.ldhb + f] = hi;
-              if (a.hb_lo) a.hb_lo[r * a.ldhb + f] = __float2bfloat16_rn(o - __bfloat162float(hi));
+              const float z = v[j] + u8[j];
+              const float coef = (c >= 1 && c <= n3 + 1) ? s : 0.f;
+              float o = (c == 0) ? y : fmaf(coef, z, (c == n3 + 1) ? lapc : 0.f);
+              o += r8[j];
+              const __nv_bfloat16 h = __float2bfloat16_rn(o);
+              const int off = c * ldb;
+              if (gok) {
+                ohg[off] = h;
+                if (olg) olg[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+              }
             }
           }
         }
@@ -402,13 +454,13 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a) {
     cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.terms < 1 || a.terms > 3 || a.nseg < 1 ||
-      a.nseg > 2)
+      a.nseg > 2 || a.mode < 0 || a.mode > 2)
     return FN_EINVAL;
   const long total = (long)a.n_tiles_n * a.n_tiles_m;
   if (total <= 0) return FN_OK;
   int grid = tc_num_sms();
   if (total < grid) grid = (int)total;
-  FN_COUNT(1), k_tc_gemm<<<grid, 192, SMEM_BYTES, s>>>(a);
+  FN_COUNT(1), k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(a);
   return FN_OK;
 }
 

@@ -19,7 +19,8 @@ struct TcGemmArgs {
   int mfeat;              // output features (M dimension)
   int tile_n;             // rows per tile: multiple of 16, <= 256
   int n_tiles_n, n_tiles_m;
-  int mode;               // 0: plain store; 1: fused forward-Laplacian tanh layer
+  int mode;               // 0: plain store; 1: fused forward-Laplacian tanh layer;
+                          // 2: value-pass layer (tanh of acc + U + b, plus residual)
   // mode 0
   float* out;
   long ldo;
@@ -30,11 +31,10 @@ struct TcGemmArgs {
   const float* U;         // per-walker term U[(r / u_div) * C + c][f], ld ldu
   long u_div;
   long ldu;
-  const float* res;       // residual (FP32, ld ldh) or null
-  float* h_out;           // FP32 output (ld ldh)
-  long ldh;
-  __nv_bfloat16* hb_hi;   // BF16 copies of the output for the next GEMM (ld ldhb)
-  __nv_bfloat16* hb_lo;   // low part (o - hi), or null
+  const __nv_bfloat16* res_hi;  // residual h^l as BF16 hi + lo (ld ldhb), or null
+  const __nv_bfloat16* res_lo;
+  __nv_bfloat16* hb_hi;   // output h^{l+1} as BF16 hi + lo: the operands of the
+  __nv_bfloat16* hb_lo;   // next GEMM and the stored activation (lo may be null)
   long ldhb;
   unsigned* status;
 };
