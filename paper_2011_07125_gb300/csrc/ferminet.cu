@@ -245,6 +245,9 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   float* Z = tc ? nullptr : ar.get<float>(rows * d1);
   __nv_bfloat16 *H0b[2] = {}, *Hab[2] = {}, *Hbb[2] = {}, *M1b[2] = {}, *M2b[2] = {};
   const long ldh0 = pad64(4 * N), ldh = pad64(d1), ldm1 = pad64(2 * max_din1), ldm2 = pad64(2 * max_din2);
+  __nv_bfloat16* Ub[2] = {};
+  if (tc && tangent)
+    for (int h = 0; h < (two ? 2 : 1); ++h) Ub[h] = ar.get<__nv_bfloat16>(Bc * C * ldh);
   if (tc) {
     for (int h = 0; h < (two ? 2 : 1); ++h) {
       H0b[h] = ar.get<__nv_bfloat16>(rows * ldh0);
@@ -282,10 +285,11 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     const __nv_bfloat16* Hcb[2] = {H0b[0], H0b[1]};
     long ldc_b = ldh0;
     const int tl = tangent ? layer_tile(C) : plain_tile(rows);
-    if (ldh != d1) {
+    if (ldh != d1) {  // padding columns must read as zeros in the MMAs
       for (int h = 0; h < (two ? 2 : 1); ++h) {
         cudaMemsetAsync(Hab[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
         cudaMemsetAsync(Hbb[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
+        if (Ub[h]) cudaMemsetAsync(Ub[h], 0, sizeof(__nv_bfloat16) * Bc * C * ldh, s);
       }
     }
     for (int l = 0; l < L; ++l) {
@@ -309,6 +313,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
                              M1b[0], M1b[1], Bc * C, l1, tu);
         u.nseg = 1;
         u.terms = c->terms;
+        u.seg_terms[0] = c->terms;
         u.rows = Bc * C;
         u.mfeat = d1;
         u.tile_n = tu;
@@ -317,6 +322,11 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         u.mode = 0;
         u.out = U;
         u.ldo = d1;
+        if (tangent) {  // stored as BF16 hi + lo: the operand of the folded segment below
+          u.hb_hi = Ub[0];
+          u.hb_lo = two ? Ub[1] : nullptr;
+          u.ldhb = ldh;
+        }
         u.bias_period = 1;
         u.status = c->d_status;
         if (!ok || tc_gemm_launch(s, u) != FN_OK) c->host_fail = true;
@@ -331,6 +341,20 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
                               c->ld_de[l], M2b[0], M2b[1], rows, l2, tl);
         m.nseg = 2;
         m.terms = c->terms;
+        m.seg_terms[0] = m.seg_terms[1] = c->terms;
+        if (tangent) {
+          // U[walker, column] enters the accumulator as a third segment: a 128 x 128
+          // identity (exact in BF16) times the walker's U rows, gathered per group
+          ok = ok && tc_make_map(&m.A[2][0], c->ident, 128, 128, 128) &&
+               tc_make_map(&m.B[2][0], Ub[0], Bc * C, ldh, C);
+          m.A[2][1] = m.A[2][0];
+          if (two) ok = ok && tc_make_map(&m.B[2][1], Ub[1], Bc * C, ldh, C);
+          else m.B[2][1] = m.B[2][0];
+          m.kblocks[2] = 2;
+          m.seg_terms[2] = two ? 2 : 1;
+          m.seg_group[2] = C;
+          m.nseg = 3;
+        }
         m.rows = rows;
         m.mfeat = d1;
         m.tile_n = tl;
@@ -341,7 +365,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         m.bias_period = C;
         m.C = C;
         m.n3 = 3 * n;
-        m.U = U;
+        m.U = tangent ? nullptr : U;
         m.u_div = (long)n * C;
         m.ldu = d1;
         m.res_hi = l >= 1 ? Hcb[0] : nullptr;
@@ -371,6 +395,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
                            Hcb[0], Hcb[1], rows, ldh, to);
       o.nseg = 1;
       o.terms = c->terms;
+      o.seg_terms[0] = c->terms;
       o.rows = rows;
       o.mfeat = (int)Ktot;
       o.tile_n = to;
@@ -909,6 +934,11 @@ fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms
     if (bad(cudaMemset(c->wb_hi, 0, sizeof(__nv_bfloat16) * off))) return FN_ECUDA;
     if (bad(cudaMemset(c->wb_lo, 0, sizeof(__nv_bfloat16) * off))) return FN_ECUDA;
     c->tc_ok = tc_encode_ready();
+    std::vector<__nv_bfloat16> eye(128 * 128, __float2bfloat16(0.f));
+    for (int i = 0; i < 128; ++i) eye[i * 128 + i] = __float2bfloat16(1.f);
+    if (bad(cudaMalloc(&c->ident, sizeof(__nv_bfloat16) * eye.size()))) return FN_ENOMEM;
+    if (bad(cudaMemcpy(c->ident, eye.data(), sizeof(__nv_bfloat16) * eye.size(), cudaMemcpyHostToDevice)))
+      return FN_ECUDA;
   }
   *out = c;
   return FN_OK;
@@ -1091,6 +1121,7 @@ void ferminet_destroy(fn_ctx* c) {
   cudaFree(c->aux);
   cudaFree(c->wb_hi);
   cudaFree(c->wb_lo);
+  cudaFree(c->ident);
   drain_profile(c);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;

@@ -211,6 +211,7 @@ struct fn_ctx {
   long wb_a[16] = {}, wb_bc[16] = {}, wb_de[16] = {}, wb_orb = 0;
   long ld_a[16] = {}, ld_bc[16] = {}, ld_de[16] = {}, ld_orb = 0;
   long wb_total = 0;
+  __nv_bfloat16* ident = nullptr;  // 128 x 128 BF16 identity (operand of the folded per-walker term)
   int force64 = 0;
   // per-class event timing
   bool prof_on = false;

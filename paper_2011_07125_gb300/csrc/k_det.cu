@@ -25,9 +25,9 @@ __device__ __forceinline__ int geo_of(const Geo& g, long wg) { return g.geo ? g.
 // lane in a[]; b[] starts as the identity row of the lane and ends as the row
 // of A^-1.  Lanes n..NM-1 hold identity padding rows.  All lanes end with the
 // same logabs, sign and pivot extremes.
-template <int NM, class T>
+template <int NM, class T, int WIDTH = 32>
 __device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane, T& logabs, T& sgn, T& pmin,
-                                        T& pmax, bool& sing) {
+                                        T& pmax, bool& sing, int nreal = 1 << 30) {
   logabs = T(0);
   sgn = T(1);
   pmin = T(INFINITY);
@@ -39,43 +39,48 @@ __device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane,
     T v = (lane >= k && lane < n) ? fabs(a[k]) : T(-1);
     int idx = lane;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      T ov = __shfl_xor_sync(FULL, v, off);
-      int oi = __shfl_xor_sync(FULL, idx, off);
+    for (int off = WIDTH / 2; off > 0; off >>= 1) {
+      T ov = __shfl_xor_sync(FULL, v, off, WIDTH);
+      int oi = __shfl_xor_sync(FULL, idx, off, WIDTH);
       if (ov > v || (ov == v && oi < idx)) {
         v = ov;
         idx = oi;
       }
     }
     const int p = idx;
-    if (p != k) {
+    // segments of one warp may differ in p: every lane takes part in the shuffles
+    if (__any_sync(FULL, p != k)) {
       const int src = lane == k ? p : (lane == p ? k : lane);
 #pragma unroll
       for (int c = 0; c < NM; ++c) {
-        a[c] = __shfl_sync(FULL, a[c], src);
-        b[c] = __shfl_sync(FULL, b[c], src);
+        a[c] = __shfl_sync(FULL, a[c], src, WIDTH);
+        b[c] = __shfl_sync(FULL, b[c], src, WIDTH);
       }
-      sgn = -sgn;
+      if (p != k) sgn = -sgn;
     }
-    const T u = __shfl_sync(FULL, a[k], k);
+    const T u = __shfl_sync(FULL, a[k], k, WIDTH);
     const T au = fabs(u);
-    pmin = fmin(pmin, au);
-    pmax = fmax(pmax, au);
-    if (!(au > T(0))) {
-      sing = true;
-      break;
+    if (k < nreal) {  // padding pivots (identity rows) do not enter the ratio
+      pmin = fmin(pmin, au);
+      pmax = fmax(pmax, au);
     }
-    logabs += log(au);
-    if (u < T(0)) sgn = -sgn;
-    const T iu = T(1) / u;
+    if (!(au > T(0))) sing = true;
+    // a singular segment keeps taking part in the shuffles (its results are
+    // discarded); the warp stops once every segment is singular
+    if (__all_sync(FULL, sing)) break;
+    if (!sing) {
+      logabs += log(au);
+      if (u < T(0)) sgn = -sgn;
+    }
+    const T iu = sing ? T(0) : T(1) / u;
     const T fct = a[k];
 #pragma unroll
     for (int c = 0; c < NM; ++c) {
       if (c >= k) {
-        T rk = __shfl_sync(FULL, a[c], k) * iu;
+        T rk = __shfl_sync(FULL, a[c], k, WIDTH) * iu;
         a[c] = (lane == k) ? rk : fma(-fct, rk, a[c]);
       }
-      T rb = __shfl_sync(FULL, b[c], k) * iu;
+      T rb = __shfl_sync(FULL, b[c], k, WIDTH) * iu;
       b[c] = (lane == k) ? rb : fma(-fct, rb, b[c]);
     }
   }
@@ -192,6 +197,97 @@ __global__ void __launch_bounds__(128) k_det_value(DetArgs a) {
   const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
   const bool flag = det_value_body<NM, float>(a, mat, m, lane, R, true);
   if (flag || a.force64) det_value_body<NM, double>(a, mat, m, lane, R, false);
+}
+
+// Value pass for NM <= 16: one warp holds the up- and down-spin matrices of one
+// (walker, determinant) in its two 16-lane halves, padded with identity rows to
+// the larger of the two sizes; the electron-nucleus distances of the walker are
+// computed once per warp into shared memory.  Matrices flagged by the FP32
+// pivot ratio are redone in FP64 by the whole warp.
+template <int NM, class T>
+__device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl, int nmax, const float* dist,
+                              bool count) {
+  T ra[NM], rb[NM];
+  const long NSS = a.nss;
+#pragma unroll
+  for (int c = 0; c < NM; ++c) {
+    ra[c] = (c == sl) ? T(1) : T(0);
+    rb[c] = (c == sl) ? T(1) : T(0);
+  }
+  if (sl < m.ns) {
+    const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
+    const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + sl) * a.N;
+#pragma unroll
+    for (int c = 0; c < NM; ++c) {
+      if (c < m.ns) {
+        const int jg = m.j0 + c;
+        const T o = (T)a.O[((m.w * a.n + jg) * (long)a.C) * a.ldo + m.q0 + sl];
+        const float* dj = dist + jg * a.N;
+        T ev = T(0);
+        for (int mm = 0; mm < a.N; ++mm) ev += (T)pi[mm] * exp(-fabs((T)sg[mm]) * (T)dj[mm]);
+        ra[c] = o * ev;
+        if (a.env) a.env[mat * NSS + sl * m.ns + c] = (float)ev;
+      }
+    }
+  }
+  T logabs, sgn, pmin, pmax;
+  bool sing;
+  warp_gj<NM, T, 16>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
+  const bool flag = !sing && pmin < (T)a.pivot_tau * pmax;
+  if (sl == 0) {
+    a.logdet[mat] = sing ? -INFINITY : (float)logabs;
+    a.sign[mat] = sing ? 0.f : (float)sgn;
+    if (count) {
+      if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
+      else if (flag) atomicAdd(a.flagged, 1ull);
+    }
+  }
+  if (a.minv && sl < m.ns) {
+#pragma unroll
+    for (int c = 0; c < NM; ++c)
+      if (c < m.ns) a.minv[mat * NSS + sl * m.ns + c] = sing ? 0.f : (float)rb[c];
+  }
+  return flag;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(128) k_det_value_pair(DetArgs a) {
+  extern __shared__ float dsh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, sl = lane & 15;
+  const long pair = (long)blockIdx.x * 4 + warp;
+  const long npair = a.Bc * a.K;
+  if (pair >= npair) return;  // warp-uniform
+  const long mat = 2 * pair + half;
+  const MatId m = mat_id(mat, a);
+  float* dist = dsh + warp * a.n * a.N;
+  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
+  for (int t = lane; t < a.n * a.N; t += 32) {
+    const int j = t / a.N, mm = t % a.N;
+    const float* xj = a.x + (m.w * a.n + j) * 3;
+    const float d0 = xj[0] - R[3 * mm], d1 = xj[1] - R[3 * mm + 1], d2 = xj[2] - R[3 * mm + 2];
+    dist[t] = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  }
+  __syncwarp();
+  const int nmax = a.n_up > a.n - a.n_up ? a.n_up : a.n - a.n_up;
+  if (m.ns == 0 && sl == 0) {
+    a.logdet[mat] = 0.f;
+    a.sign[mat] = 1.f;
+  }
+  bool flag = false;
+  // an empty spin channel (ns = 0) still takes part in the warp-wide shuffles
+  flag = det_pair_body<NM, float>(a, mat, m, sl, nmax, dist, true) && m.ns > 0;
+  if (m.ns == 0 && sl == 0) {
+    a.logdet[mat] = 0.f;
+    a.sign[mat] = 1.f;
+  }
+  if (__any_sync(FULL, flag || a.force64)) {
+    det_pair_body<NM, double>(a, mat, m, sl, nmax, dist, false);
+    if (m.ns == 0 && sl == 0) {
+      a.logdet[mat] = 0.f;
+      a.sign[mat] = 1.f;
+    }
+  }
 }
 
 template <int NM, class T>
@@ -362,6 +458,10 @@ void launch_nm(cudaStream_t s, const DetArgs& a) {
       attr = true;
     }
     FN_COUNT(1), k_det_tangent<NM><<<(unsigned)nmat, 128, smem, s>>>(a);
+  } else if (NM <= 16 && (long)a.n * a.N * 4 * sizeof(float) <= 32768) {
+    const long npair = a.Bc * a.K;
+    FN_COUNT(1), k_det_value_pair<NM <= 16 ? NM : 16><<<(unsigned)((npair + 3) / 4), 128,
+                                                         sizeof(float) * 4 * a.n * a.N, s>>>(a);
   } else {
     FN_COUNT(1), k_det_value<NM><<<(unsigned)((nmat + 3) / 4), 128, 0, s>>>(a);
   }

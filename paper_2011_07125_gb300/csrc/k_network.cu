@@ -78,144 +78,100 @@ __global__ void k_feat2(const float* __restrict__ x, long Bc, int n, int Q, floa
   *reinterpret_cast<float4*>(out + 16) = make_float4(0.f, 0.f, 0.f, 4.f * ir);
 }
 
-// M1[w][c][s*din + f] = mean over electrons i of spin s of H[w][i][c][f].
-__global__ void k_mean1(const float* __restrict__ H, long Bc, int n, int n_up, int C, int din,
-                        float* __restrict__ M1) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long tot = Bc * C * 2 * din;
-  if (idx >= tot) return;
-  int f = (int)(idx % din);
-  long r = idx / din;
-  int s = (int)(r % 2);
-  long wc = r / 2;
-  int c = (int)(wc % C);
-  long w = wc / C;
-  int i0 = s == 0 ? 0 : n_up, i1 = s == 0 ? n_up : n;
-  float acc = 0.f;
-  for (int i = i0; i < i1; ++i) acc += H[((w * n + i) * C + c) * din + f];
-  M1[idx] = i1 > i0 ? acc / (float)(i1 - i0) : 0.f;
-}
-
-// M2[w][i][c][s*din2 + f]: mean over electrons j of spin s of h_ij, expanded
-// to the dense column layout.  With T the derivative of h_ij along r_i,
-// d/dr_e mean_j h_ij = (1/n_s) sum_j T_ij for e = i, -(1/n_s) T_ie for e != i
-// of spin s, and 0 otherwise; the Laplacian column is the mean of the
-// two-electron Laplacians.
-__global__ void k_mean2(const float* __restrict__ E, long Bc, int n, int n_up, int Q, int din2, int C,
-                        float* __restrict__ M2) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long tot = Bc * n * C * 2 * din2;
-  if (idx >= tot) return;
-  int f = (int)(idx % din2);
-  long r = idx / din2;
-  int s = (int)(r % 2);
-  r /= 2;
-  int c = (int)(r % C);
-  long wi = r / C;
-  int i = (int)(wi % n);
-  long w = wi / n;
-  int j0 = s == 0 ? 0 : n_up, j1 = s == 0 ? n_up : n;
-  int ns = j1 - j0;
-  float out = 0.f;
-  if (ns > 0) {
-    const float* Ei = E + (w * n + i) * (long)n * Q * din2;
-    const float inv = 1.f / (float)ns;
-    const int n3 = 3 * n;
-    if (c == 0) {
-      float a = 0.f;
-      for (int j = j0; j < j1; ++j) a += Ei[(long)j * Q * din2 + f];
-      out = a * inv;
-    } else if (Q > 1 && c <= n3) {
-      int e = (c - 1) / 3, dd = (c - 1) % 3;
-      if (e == i) {
-        float a = 0.f;
-        for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 1 + dd) * din2 + f];
-        out = a * inv;
-      } else if (e >= j0 && e < j1) {
-        out = -Ei[((long)e * Q + 1 + dd) * din2 + f] * inv;
-      }
-    } else if (Q > 1 && c == n3 + 1) {
-      float a = 0.f;
-      for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 4) * din2 + f];
-      out = a * inv;
-    }
-  }
-  M2[idx] = out;
-}
-
-// Dense-column spin means of the two-electron stream (see k_mean2), written
-// as BF16 hi / lo parts for the tensor-core GEMM; padding columns are zeroed.
-__global__ void k_mean2_bf16(const float* __restrict__ E, long Bc, int n, int n_up, int Q, int din2, int C,
-                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long ldb) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long tot = Bc * n * C * ldb;
-  if (idx >= tot) return;
-  const int col = (int)(idx % ldb);
-  long r = idx / ldb;
-  float out = 0.f;
-  if (col < 2 * din2) {
-    const int s = col / din2, f = col % din2;
-    const int c = (int)(r % C);
-    const long wi = r / C;
-    const int i = (int)(wi % n);
-    const long w = wi / n;
+// Dense-column spin means of the two-electron stream, one block per
+// (walker, electron i): the pair rows h_ij (all j, all Q quantities) are staged
+// in shared memory with the per-spin sums, then the C x ldb output block is
+// written with 32-bit indexing.  Output as FP32 (out32) or BF16 hi / lo (lo may
+// be null); columns 2 din2 .. ldb-1 are zero.  Column layout as in k_mean2.
+template <int MAXN>
+__global__ void __launch_bounds__(256) k_mean2_rows(const float* __restrict__ E, int n, int n_up, int Q, int din2,
+                                                    int C, float* __restrict__ out32, __nv_bfloat16* __restrict__ hi,
+                                                    __nv_bfloat16* __restrict__ lo, int ldb) {
+  extern __shared__ float sh[];
+  float* Es = sh;                              // [n][Q][din2]
+  float* Ss = sh + MAXN * kQ * 32;             // [2][Q][din2] per-spin sums
+  const long wi = blockIdx.x;
+  const int i = (int)(wi % n);
+  const int QD = Q * din2;
+  const float* src = E + wi * (long)n * QD;
+  for (int t = threadIdx.x; t < n * QD; t += blockDim.x) Es[t] = src[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * QD; t += blockDim.x) {
+    const int s = t / QD, qf = t % QD;
     const int j0 = s == 0 ? 0 : n_up, j1 = s == 0 ? n_up : n;
-    const int ns = j1 - j0;
-    if (ns > 0) {
-      const float* Ei = E + (w * n + i) * (long)n * Q * din2;
-      const float inv = 1.f / (float)ns;
-      const int n3 = 3 * n;
-      if (c == 0) {
-        float a = 0.f;
-        for (int j = j0; j < j1; ++j) a += Ei[(long)j * Q * din2 + f];
-        out = a * inv;
-      } else if (Q > 1 && c <= n3) {
-        const int e = (c - 1) / 3, dd = (c - 1) % 3;
-        if (e == i) {
-          float a = 0.f;
-          for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 1 + dd) * din2 + f];
-          out = a * inv;
-        } else if (e >= j0 && e < j1) {
-          out = -Ei[((long)e * Q + 1 + dd) * din2 + f] * inv;
+    float a = 0.f;
+    for (int j = j0; j < j1; ++j) a += Es[j * QD + qf];
+    Ss[t] = a;
+  }
+  __syncthreads();
+  const int n3 = 3 * n;
+  const int tot = C * ldb;
+  const long obase = wi * (long)tot;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int c = t / ldb, col = t % ldb;
+    float v = 0.f;
+    if (col < 2 * din2) {
+      const int s = col / din2, f = col % din2;
+      const int j0 = s == 0 ? 0 : n_up, j1 = s == 0 ? n_up : n;
+      const int ns = j1 - j0;
+      if (ns > 0) {
+        const float inv = 1.f / (float)ns;
+        if (c == 0) {
+          v = Ss[s * QD + f] * inv;
+        } else if (Q > 1 && c <= n3) {
+          const int e = (c - 1) / 3, dd = (c - 1) % 3;
+          if (e == i) v = Ss[s * QD + (1 + dd) * din2 + f] * inv;
+          else if (e >= j0 && e < j1) v = -Es[e * QD + (1 + dd) * din2 + f] * inv;
+        } else if (Q > 1 && c == n3 + 1) {
+          v = Ss[s * QD + 4 * din2 + f] * inv;
         }
-      } else if (Q > 1 && c == n3 + 1) {
-        float a = 0.f;
-        for (int j = j0; j < j1; ++j) a += Ei[((long)j * Q + 4) * din2 + f];
-        out = a * inv;
       }
     }
+    if (out32) {
+      out32[obase + t] = v;
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[obase + t] = h;
+      if (lo) lo[obase + t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
-  const __nv_bfloat16 h = __float2bfloat16_rn(out);
-  hi[idx] = h;
-  if (lo) lo[idx] = __float2bfloat16_rn(out - __bfloat162float(h));
 }
 
-// Spin means of a one-electron activation held as BF16 hi + lo (row stride
-// ldin), written as BF16 hi + lo with row stride ldout (padding zeroed):
-// out[w][c][s*din + f] = mean over electrons i of spin s of (hi + lo)[w][i][c][f].
-__global__ void k_mean1_bf16(const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo, long ldin,
-                             long Bc, int n, int n_up, int C, int din, __nv_bfloat16* __restrict__ ohi,
-                             __nv_bfloat16* __restrict__ olo, long ldout) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Bc * C * ldout) return;
-  const int col = (int)(idx % ldout);
-  const long wc = idx / ldout;
-  const int c = (int)(wc % C);
+// Spin means of a one-electron activation, one block per (walker, column c):
+// out[w][c][s*din + f] = mean over electrons i of spin s of H[w][i][c][f], H
+// either FP32 (h32, row stride ldin) or BF16 hi + lo; output FP32 (out32,
+// stride ldout) or BF16 hi / lo (stride ldout, padding zeroed).
+__global__ void __launch_bounds__(256) k_mean1_rows(const float* __restrict__ h32,
+                                                    const __nv_bfloat16* __restrict__ hhi,
+                                                    const __nv_bfloat16* __restrict__ hlo, int ldin, int n, int n_up,
+                                                    int C, int din, float* __restrict__ out32,
+                                                    __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo,
+                                                    int ldout) {
+  const long wc = blockIdx.x;
   const long w = wc / C;
-  float out = 0.f;
-  if (col < 2 * din) {
-    const int s = col / din, f = col % din;
-    const int i0 = s == 0 ? 0 : n_up, i1 = s == 0 ? n_up : n;
-    float acc = 0.f;
-    for (int i = i0; i < i1; ++i) {
-      const long r = ((w * n + i) * C + c) * ldin + f;
-      acc += __bfloat162float(hi[r]) + (lo ? __bfloat162float(lo[r]) : 0.f);
+  const int c = (int)(wc % C);
+  const long rowc = (w * n) * (long)C + c;  // row of electron 0, column c
+  const long ob = wc * (long)ldout;
+  for (int col = threadIdx.x; col < ldout; col += blockDim.x) {
+    float v = 0.f;
+    if (col < 2 * din) {
+      const int s = col / din, f = col % din;
+      const int i0 = s == 0 ? 0 : n_up, i1 = s == 0 ? n_up : n;
+      float a = 0.f;
+      for (int i = i0; i < i1; ++i) {
+        const long r = (rowc + (long)i * C) * ldin + f;
+        a += h32 ? h32[r] : __bfloat162float(hhi[r]) + (hlo ? __bfloat162float(hlo[r]) : 0.f);
+      }
+      v = i1 > i0 ? a / (float)(i1 - i0) : 0.f;
     }
-    out = i1 > i0 ? acc / (float)(i1 - i0) : 0.f;
+    if (out32) {
+      out32[ob + col] = v;
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      ohi[ob + col] = h;
+      if (olo) olo[ob + col] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
-  const __nv_bfloat16 h = __float2bfloat16_rn(out);
-  ohi[idx] = h;
-  if (olo) olo[idx] = __float2bfloat16_rn(out - __bfloat162float(h));
 }
 
 __global__ void k_split_bf16(const float* __restrict__ src, long src_ld, long rows, long cols,
@@ -262,49 +218,65 @@ __global__ void k_tanh_fl(const float* __restrict__ Z, const float* __restrict__
 // read as broadcasts.  The Laplacian rule uses |dz|^2 = 2 |dz/dr_i|^2 because
 // dz/dr_j = -dz/dr_i.
 template <int DIN>
+__device__ __forceinline__ void two_layer_pair(const float (&wr)[DIN], float bias, const float* sh, long p, int Q,
+                                               int d2, int f, int residual, float* __restrict__ Eout,
+                                               float* __restrict__ Y2) {
+  float z[kQ] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < DIN; ++k) {
+    z[0] = fmaf(wr[k], sh[k], z[0]);
+    if (Q > 1) {
+#pragma unroll
+      for (int q = 1; q < kQ; ++q) z[q] = fmaf(wr[k], sh[q * DIN + k], z[q]);
+    }
+  }
+  if (f >= d2) return;
+  z[0] += bias;
+  const float y = tanhf(z[0]);
+  const float s = 1.f - y * y;
+  if (Y2) Y2[p * d2 + f] = y;
+  float* out = Eout + p * Q * d2;
+  out[f] = y + (residual ? sh[f] : 0.f);
+  if (Q > 1) {
+    const float sq = z[1] * z[1] + z[2] * z[2] + z[3] * z[3];
+#pragma unroll
+    for (int q = 1; q <= 3; ++q) out[q * d2 + f] = s * z[q] + (residual ? sh[q * DIN + f] : 0.f);
+    out[4 * d2 + f] = s * z[4] - 4.f * y * s * sq + (residual ? sh[4 * DIN + f] : 0.f);
+  }
+}
+
+// Two-electron layer h_ij -> tanh(W h_ij + c) (+ h_ij).  One warp handles two
+// pairs per iteration (grid-stride over pairs), lane f = output feature, its row
+// of W held in registers; the pairs' Q x DIN input rows are staged in shared
+// memory and read as broadcasts.  The Laplacian rule uses |dz|^2 = 2 |dz/dr_i|^2
+// because dz/dr_j = -dz/dr_i.
+template <int DIN>
 __global__ void __launch_bounds__(256) k_two_layer(const float* __restrict__ Ein, long pairs, int Q, int din2,
                                                    int d2, const float* __restrict__ W,
                                                    const float* __restrict__ cb, int residual,
                                                    float* __restrict__ Eout, float* __restrict__ Y2) {
-  __shared__ __align__(16) float in_s[8][kQ * DIN];
+  __shared__ __align__(16) float in_s[8][2][kQ * DIN];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int f = lane;
   float wr[DIN];
 #pragma unroll
   for (int k = 0; k < DIN; ++k) wr[k] = (f < d2 && k < din2) ? W[(long)f * din2 + k] : 0.f;
   const float bias = f < d2 ? cb[f] : 0.f;
-  float* sh = in_s[wib];
   const long nwarps = (long)gridDim.x * 8;
-  for (long p = (long)blockIdx.x * 8 + wib; p < pairs; p += nwarps) {
-    const float* in = Ein + p * Q * din2;
-    for (int t = lane; t < Q * DIN; t += 32) {
+  const int QD = Q * DIN;
+  for (long p0 = (long)blockIdx.x * 8 + wib; p0 < pairs; p0 += 2 * nwarps) {
+    const long p1 = p0 + nwarps;
+    const bool has1 = p1 < pairs;
+    const float* in0 = Ein + p0 * Q * din2;
+    const float* in1 = Ein + p1 * Q * din2;
+    for (int t = lane; t < QD; t += 32) {
       const int q = t / DIN, k = t % DIN;
-      sh[t] = k < din2 ? in[q * din2 + k] : 0.f;
+      in_s[wib][0][t] = k < din2 ? in0[q * din2 + k] : 0.f;
+      in_s[wib][1][t] = (has1 && k < din2) ? in1[q * din2 + k] : 0.f;
     }
     __syncwarp();
-    float z[kQ] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < DIN; ++k) {
-      z[0] = fmaf(wr[k], sh[k], z[0]);
-      if (Q > 1) {
-#pragma unroll
-        for (int q = 1; q < kQ; ++q) z[q] = fmaf(wr[k], sh[q * DIN + k], z[q]);
-      }
-    }
-    if (f < d2) {
-      z[0] += bias;
-      const float y = tanhf(z[0]);
-      const float s = 1.f - y * y;
-      if (Y2) Y2[p * d2 + f] = y;
-      float* out = Eout + p * Q * d2;
-      out[f] = y + (residual ? sh[f] : 0.f);
-      if (Q > 1) {
-        const float sq = z[1] * z[1] + z[2] * z[2] + z[3] * z[3];
-#pragma unroll
-        for (int q = 1; q <= 3; ++q) out[q * d2 + f] = s * z[q] + (residual ? sh[q * DIN + f] : 0.f);
-        out[4 * d2 + f] = s * z[4] - 4.f * y * s * sq + (residual ? sh[4 * DIN + f] : 0.f);
-      }
-    }
+    two_layer_pair<DIN>(wr, bias, in_s[wib][0], p0, Q, d2, f, residual, Eout, Y2);
+    if (has1) two_layer_pair<DIN>(wr, bias, in_s[wib][1], p1, Q, d2, f, residual, Eout, Y2);
     __syncwarp();
   }
 }
@@ -322,26 +294,30 @@ void launch_features(cudaStream_t s, const float* x, long Bc, long w0, int n, in
 }
 
 void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int C, int din, float* M1) {
-  long tot = Bc * C * 2 * din;
-  if (tot > 0) FN_COUNT(1), k_mean1<<<nblk(tot, 256), 256, 0, s>>>(H, Bc, n, n_up, C, din, M1);
+  if (Bc * C <= 0) return;
+  FN_COUNT(1), k_mean1_rows<<<(unsigned)(Bc * C), 256, 0, s>>>(H, nullptr, nullptr, din, n, n_up, C, din, M1, nullptr,
+                                                               nullptr, 2 * din);
 }
 
 void launch_mean2(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C, float* M2) {
-  long tot = Bc * n * C * 2 * din2;
-  if (tot > 0) FN_COUNT(1), k_mean2<<<nblk(tot, 256), 256, 0, s>>>(E, Bc, n, n_up, Q, din2, C, M2);
+  if (Bc * n <= 0) return;
+  const size_t smem = sizeof(float) * (64 * kQ * 32 + 2 * kQ * 32);
+  FN_COUNT(1), k_mean2_rows<64><<<(unsigned)(Bc * n), 256, smem, s>>>(E, n, n_up, Q, din2, C, M2, nullptr, nullptr,
+                                                                      2 * din2);
 }
 
 void launch_mean2_bf16(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C,
                        __nv_bfloat16* hi, __nv_bfloat16* lo, long ldb) {
-  long tot = Bc * n * C * ldb;
-  if (tot > 0) FN_COUNT(1), k_mean2_bf16<<<nblk(tot, 256), 256, 0, s>>>(E, Bc, n, n_up, Q, din2, C, hi, lo, ldb);
+  if (Bc * n <= 0) return;
+  const size_t smem = sizeof(float) * (64 * kQ * 32 + 2 * kQ * 32);
+  FN_COUNT(1), k_mean2_rows<64><<<(unsigned)(Bc * n), 256, smem, s>>>(E, n, n_up, Q, din2, C, nullptr, hi, lo, (int)ldb);
 }
 
 void launch_mean1_bf16(cudaStream_t s, const __nv_bfloat16* hi, const __nv_bfloat16* lo, long ldin, long Bc, int n,
                        int n_up, int C, int din, __nv_bfloat16* ohi, __nv_bfloat16* olo, long ldout) {
-  long tot = Bc * C * ldout;
-  if (tot > 0)
-    FN_COUNT(1), k_mean1_bf16<<<nblk(tot, 256), 256, 0, s>>>(hi, lo, ldin, Bc, n, n_up, C, din, ohi, olo, ldout);
+  if (Bc * C <= 0) return;
+  FN_COUNT(1), k_mean1_rows<<<(unsigned)(Bc * C), 256, 0, s>>>(nullptr, hi, lo, (int)ldin, n, n_up, C, din, nullptr, ohi,
+                                                               olo, (int)ldout);
 }
 
 void launch_split_bf16(cudaStream_t s, const float* src, long src_ld, long rows, long cols, __nv_bfloat16* hi,

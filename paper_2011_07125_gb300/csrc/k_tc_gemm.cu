@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         bool ok = true;
         for (int sg = 0; sg < a.nseg && ok; ++sg)
           for (int kb = 0; kb < a.kblocks[sg] && ok; ++kb)
-            for (int t = 0; t < a.terms && ok; ++t) {
+            for (int t = 0; t < a.seg_terms[sg] && ok; ++t) {
               if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status)) {
                 ok = false;
                 break;
@@ -208,8 +208,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
               uint8_t* sa = smem + stage * STAGE_BYTES;
               uint8_t* sb = sa + A_BYTES;
               mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
-              tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
-              tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
+              if (a.seg_group[sg] == 0) {
+                tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
+                tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
+              } else {
+                // identity weights for this m-tile's 64-feature block; B rows
+                // gathered per group from the per-walker tensor
+                const int G = a.seg_group[sg];
+                tma_load_2d(sa, &a.A[sg][ai], kb * BK, 0, &full[stage]);
+                for (int g0 = 0; g0 < tile_n; g0 += G) {
+                  long r0 = (long)tn * tile_n + g0;
+                  if (r0 >= a.rows) r0 = a.rows - G;  // past the end: any in-range rows (unused)
+                  const int y = (int)((r0 / a.u_div) * G);
+                  tma_load_2d(sb + (size_t)g0 * BK * 2, &a.B[sg][bi], tm * BM + kb * BK, y, &full[stage]);
+                }
+              }
               if (++stage == STAGES) {
                 stage = 0;
                 phase ^= 1;
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         uint32_t first = 1;
         for (int sg = 0; sg < a.nseg && ok; ++sg)
           for (int kb = 0; kb < a.kblocks[sg] && ok; ++kb)
-            for (int t = 0; t < a.terms && ok; ++t) {
+            for (int t = 0; t < a.seg_terms[sg] && ok; ++t) {
               if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
                 ok = false;
                 break;
@@ -316,12 +329,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       } else if (a.mode == 0) {
         const float bf = (fok && bias) ? bias[f] : 0.f;
         for (int c0 = half * 8; c0 < tile_n; c0 += 16) {
+          if (r_tile + c0 >= a.rows) break;  // warp-uniform
           float v[8];
           tmem_ld8(tbase + c0, v);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const long r = r_tile + c0 + j;
-            if (fok && r < a.rows) out[r * a.ldo + f] = v[j] + ((r % a.bias_period) == 0 ? bf : 0.f);
+            if (!(fok && r < a.rows)) continue;
+            const float o = v[j] + ((r % a.bias_period) == 0 ? bf : 0.f);
+            if (oh) {
+              const __nv_bfloat16 h = __float2bfloat16_rn(o);
+              oh[r * a.ldhb + f] = h;
+              if (ol) ol[r * a.ldhb + f] = __float2bfloat16_rn(o - __bfloat162float(h));
+            } else {
+              out[r * a.ldo + f] = o;
+            }
           }
         }
       } else {
@@ -334,14 +356,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
           if (r0 >= a.rows) continue;  // warp-uniform: no TMEM access for groups past the end
           const bool gok = fok;       // per lane: loads and stores only
           // per-group base pointers; column offsets below fit in 32 bits
-          const float* __restrict__ ug = Up + ((r0 / a.u_div) * C) * (long)ldu + (fok ? f : 0);
+          const float* __restrict__ ug = Up ? Up + ((r0 / a.u_div) * C) * (long)ldu + (fok ? f : 0) : nullptr;
           const long rb = r0 * (long)ldb + (fok ? f : 0);
-          // pass 1: value column and sum of squared tangents
+          // pass 1: value column and sum of squared tangents (TMEM only when U
+          // was accumulated by the MMA)
           float z0 = 0.f, sq = 0.f;
           for (int c0 = 0; c0 < C; c0 += 8) {
             float u8[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) u8[j] = gok ? ug[(c0 + j) * ldu] : 0.f;
+            for (int j = 0; j < 8; ++j) u8[j] = (gok && ug) ? ug[(c0 + j) * ldu] : 0.f;
             float v[8];
             tmem_ld8(tbase + gi * C + c0, v);
 #pragma unroll
@@ -359,32 +382,45 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
           const __nv_bfloat16* __restrict__ rlg = rl ? rl + rb : nullptr;
           __nv_bfloat16* __restrict__ ohg = oh + rb;
           __nv_bfloat16* __restrict__ olg = ol ? ol + rb : nullptr;
-          // pass 2: outputs (+ residual), stored as BF16 hi + lo
-          for (int c0 = 0; c0 < C; c0 += 8) {
-            float u8[8], r8[8];
+          // pass 2: outputs (+ residual), stored as BF16 hi + lo; the global
+          // loads of the next 8-column chunk are issued before the current
+          // chunk is processed
+          auto load8 = [&](float (&r8)[8], int c0) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int off = (c0 + j) * ldb;
-              u8[j] = gok ? ug[(c0 + j) * ldu] : 0.f;
-              r8[j] = (gok && rhg) ? __bfloat162float(rhg[off]) : 0.f;
-              if (gok && rlg) r8[j] += __bfloat162float(rlg[off]);
+              float v = 0.f;
+              if (gok && rhg) v += __bfloat162float(rhg[off]);
+              if (gok && rlg) v += __bfloat162float(rlg[off]);
+              r8[j] = v;
             }
+          };
+          auto emit8 = [&](const float (&r8)[8], int c0) {
             float v[8];
             tmem_ld8(tbase + gi * C + c0, v);
+            if (!gok) return;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int c = c0 + j;
-              const float z = v[j] + u8[j];
               const float coef = (c >= 1 && c <= n3 + 1) ? s : 0.f;
+              const float z = v[j] + (ug ? ug[c * ldu] : 0.f);
               float o = (c == 0) ? y : fmaf(coef, z, (c == n3 + 1) ? lapc : 0.f);
-              o += r8[j];
+              o += r8[j];  // residual
               const __nv_bfloat16 h = __float2bfloat16_rn(o);
               const int off = c * ldb;
-              if (gok) {
-                ohg[off] = h;
-                if (olg) olg[off] = __float2bfloat16_rn(o - __bfloat162float(h));
-              }
+              ohg[off] = h;
+              if (olg) olg[off] = __float2bfloat16_rn(o - __bfloat162float(h));
             }
+          };
+          float ra[8], rbuf[8];
+          load8(ra, 0);
+          for (int c0 = 0; c0 < C; c0 += 16) {
+            const bool second = c0 + 8 < C;
+            if (second) load8(rbuf, c0 + 8);
+            emit8(ra, c0);
+            if (!second) break;
+            if (c0 + 16 < C) load8(ra, c0 + 16);
+            emit8(rbuf, c0 + 8);
           }
         }
       }
@@ -453,9 +489,12 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a) {
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
-  if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.terms < 1 || a.terms > 3 || a.nseg < 1 ||
-      a.nseg > 2 || a.mode < 0 || a.mode > 2)
+  if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.nseg < 1 || a.nseg > 3 || a.mode < 0 || a.mode > 2)
     return FN_EINVAL;
+  for (int sg = 0; sg < a.nseg; ++sg) {
+    if (a.seg_terms[sg] < 1 || a.seg_terms[sg] > 3 || a.kblocks[sg] < 1) return FN_EINVAL;
+    if (a.seg_group[sg] && (a.seg_group[sg] % 8 || a.tile_n % a.seg_group[sg] || a.u_div < 1)) return FN_EINVAL;
+  }
   const long total = (long)a.n_tiles_n * a.n_tiles_m;
   if (total <= 0) return FN_OK;
   int grid = tc_num_sms();
@@ -475,6 +514,7 @@ extern "C" fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, f
   a.A[0][1] = a.A[0][0];
   a.B[0][1] = a.B[0][0];
   a.kblocks[0] = K / BK;
+  a.seg_terms[0] = 1;
   a.nseg = 1;
   a.terms = 1;
   a.rows = N;

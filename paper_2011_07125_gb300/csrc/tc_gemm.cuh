@@ -11,9 +11,12 @@ namespace fn {
 struct TcGemmArgs {
   // A[seg][hi|lo]: weights [mfeat][K_seg] bf16 (K-major, padded to 64)
   // B[seg][hi|lo]: activations [rows][K_seg] bf16 (K-major, padded to 64)
-  CUtensorMap A[2][2];
-  CUtensorMap B[2][2];
-  int kblocks[2];
+  CUtensorMap A[3][2];
+  CUtensorMap B[3][2];
+  int kblocks[3];
+  int seg_terms[3];       // per segment: 1: hi*hi; 2: + hi*lo; 3: + lo*hi
+  int seg_group[3];       // 0: B rows contiguous; C: B tile gathered per group of C
+                          // rows from row (r0 / u_div) * C of the segment's tensor
   int nseg, terms;        // terms 1: hi*hi; 3: hi*hi + hi*lo + lo*hi
   long rows;              // activation rows (N dimension)
   int mfeat;              // output features (M dimension)
@@ -21,14 +24,15 @@ struct TcGemmArgs {
   int n_tiles_n, n_tiles_m;
   int mode;               // 0: plain store; 1: fused forward-Laplacian tanh layer;
                           // 2: value-pass layer (tanh of acc + U + b, plus residual)
-  // mode 0
+  // mode 0 (FP32 out, or BF16 hi/lo into hb_hi/hb_lo with ld ldhb when hb_hi is set)
   float* out;
   long ldo;
   const float* bias;      // added on rows with r % bias_period == 0 (value rows)
   int bias_period;
   // mode 1 (rows in groups of C columns; tile_n a multiple of C)
   int C, n3;
-  const float* U;         // per-walker term U[(r / u_div) * C + c][f], ld ldu
+  const float* U;         // per-walker term U[(r / u_div) * C + c][f], ld ldu (null when
+                          // U is accumulated by an extra segment instead)
   long u_div;
   long ldu;
   const __nv_bfloat16* res_hi;  // residual h^l as BF16 hi + lo (ld ldhb), or null
