@@ -184,7 +184,35 @@ def run_reference(args, wl):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def tangent_roofline(fn, prec, clocks, pk, pk_kind):
+def kernel_source_hash() -> str:
+    """Hash of the sources of the timed GEMM class (tensor-core and SIMT GEMMs
+    and the schedule that sizes their launches)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_tc_gemm.cu", "tc_gemm.cuh", "k_gemm.cu", "ferminet.cu"):
+        with open(os.path.join(ROOT, "paper_2011_07125_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, prec: str):
+    """DRAM bytes per walker of the timed GEMM class from the committed ncu
+    summary (profiles/roofline_traffic.md), or None if the kernel sources have
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        if not line.startswith("traffic:"):
+            continue
+        kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+        if kv.get("workload") == workload and kv.get("precision") == prec and kv.get("source") == src:
+            return float(kv["bytes_per_walker"])
+    return None
+
+
+def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_launch=None):
     r = fn.profile_read("tangent_gemm")
     if r["launches"] == 0 or r["ms"] <= 0:
         return None
@@ -196,8 +224,11 @@ def tangent_roofline(fn, prec, clocks, pk, pk_kind):
     else:
         peak = _num(pk, "bf16_tflops_sustained", "bf16_tflops") or 1700.0
         bound, note = "tensor", f"bf16 sustained, {pk_kind}"
+    bpw = recorded_traffic(workload, prec) if workload else None
+    traffic = bpw * walkers_per_launch if (bpw is not None and walkers_per_launch) else None
     return {"bound": bound, "kernel": "layer + orbital GEMMs of the local-energy pass", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
             "launches": r["launches"], "avg_launch_ms": r["ms"] / r["launches"], "peak_note": note}
 
 
@@ -216,7 +247,7 @@ def run_gpu(args, wl):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    prec = args.precision or "fp32"
+    prec = args.precision or wl.precision
     fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision=prec)
     P = synth.init_params(fn.layout)
     x0 = synth.init_walkers(wl, synth.SEED_WALKERS + rank)
@@ -262,7 +293,11 @@ def run_gpu(args, wl):
     clocks = cs.summary()
     st = fn.sync()
     pk, pk_kind = peaks()
-    roof = tangent_roofline(fn, prec, clocks, pk, pk_kind)
+    r_tg = fn.profile_read("tangent_gemm")
+    passes = args.steps  # one local-energy pass per step
+    launches_per_pass = max(1, r_tg["launches"] // max(passes, 1))
+    roof = tangent_roofline(fn, prec, clocks, pk, pk_kind, wl.name,
+                            wl.batch * passes / max(r_tg["launches"], 1))
     classes = {k: fn.profile_read(k) for k in ("tangent_gemm", "det_tangent", "two_layer", "means", "tanh",
                                                  "value_pass", "adjoint")}
     fn.profile(False)

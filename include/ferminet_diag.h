@@ -15,12 +15,14 @@ extern "C" {
  * pass (mixed precision), in its plain-store mode:
  *   C[n][m] = sum_k A[m][k] * B[n][k]   (FP32 accumulation in tensor memory)
  * d_A: [M][K] bf16, d_B: [N][K] bf16 (both row-major, K a multiple of 64,
- * 16-byte aligned); d_C: [N][M] float32.  tile_n: rows of B per tile (a multiple
- * of 16, 16..256).  d_status: a device word; the value 4 is OR-ed into it if a bounded wait
+ * 16-byte aligned); d_C: [N][M] float32.  rows_on_lanes = 0: A rows on the MMA M
+ * dimension (TMEM lanes) and tile_n rows of B per tile; rows_on_lanes = 1: B rows
+ * on the lanes and tile_n rows of A per tile (the orientation of the plain and
+ * value-pass GEMMs; M a multiple of 4).  tile_n: a multiple of 16, 16..256.  d_status: a device word; the value 4 is OR-ed into it if a bounded wait
  * inside the kernel timed out.  Asynchronous on `stream`.  FN_EINVAL for bad
  * shapes or if the tensor-map encoder is unavailable. */
 fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, float* d_C, int M, int N, int K, int tile_n,
-                                  void* stream, unsigned* d_status);
+                                  int rows_on_lanes, void* stream, unsigned* d_status);
 
 #ifdef __cplusplus
 }

@@ -174,6 +174,30 @@ Geo geo_of(fn_ctx* c) { return Geo{c->d_R, c->d_Z, c->d_Enn64, c->G > 1 ? c->d_g
 
 inline long pad64(long v) { return ((v + 63) / 64) * 64; }
 
+// Rows-on-lanes orientation: activations as the A operand (128 rows per tile)
+// and weights as B (features per tile = tile_n).
+bool tc_segment_rm(TcGemmArgs& g, int seg, const __nv_bfloat16* x_hi, const __nv_bfloat16* x_lo, long rows, long lda,
+                   const __nv_bfloat16* w_hi, const __nv_bfloat16* w_lo, long mfeat, long ldw, int tile_n) {
+  if (ldw != lda) return false;
+  bool ok = tc_make_map(&g.A[seg][0], x_hi, rows, lda, 128) && tc_make_map(&g.B[seg][0], w_hi, mfeat, ldw, tile_n);
+  if (w_lo && x_lo)
+    ok = ok && tc_make_map(&g.A[seg][1], x_lo, rows, lda, 128) && tc_make_map(&g.B[seg][1], w_lo, mfeat, ldw, tile_n);
+  else {
+    g.A[seg][1] = g.A[seg][0];
+    g.B[seg][1] = g.B[seg][0];
+  }
+  g.kblocks[seg] = (int)(lda / 64);
+  return ok;
+}
+
+// Features per tile in the rows-on-lanes orientation (<= 256, multiple of 16).
+int feature_tile(long mfeat, int* n_tiles) {
+  const long nt = (mfeat + 255) / 256;
+  const long per = (mfeat + nt - 1) / nt;
+  *n_tiles = (int)nt;
+  return (int)(((per + 15) / 16) * 16);
+}
+
 // Rows per tile of the fused layer epilogue: whole (walker, electron) groups of
 // C columns, at most 256 rows, a multiple of 16.
 int layer_tile(int C) {
@@ -308,17 +332,19 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
       {
         Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * d1 * 2.0 * a1);
         TcGemmArgs u{};
-        const int tu = plain_tile(Bc * C);
-        bool ok = tc_segment(u, 0, c->wb_hi + c->wb_bc[l], two ? c->wb_lo + c->wb_bc[l] : nullptr, d1, c->ld_bc[l],
-                             M1b[0], M1b[1], Bc * C, l1, tu);
+        int ntf = 1;
+        const int tu = feature_tile(d1, &ntf);
+        bool ok = tc_segment_rm(u, 0, M1b[0], M1b[1], Bc * C, l1, c->wb_hi + c->wb_bc[l],
+                                two ? c->wb_lo + c->wb_bc[l] : nullptr, d1, c->ld_bc[l], tu);
+        u.rm = 1;
         u.nseg = 1;
         u.terms = c->terms;
         u.seg_terms[0] = c->terms;
         u.rows = Bc * C;
         u.mfeat = d1;
         u.tile_n = tu;
-        u.n_tiles_n = (int)((Bc * C + tu - 1) / tu);
-        u.n_tiles_m = (d1 + 127) / 128;
+        u.n_tiles_n = ntf;
+        u.n_tiles_m = (int)((Bc * C + 127) / 128);
         u.mode = 0;
         u.out = U;
         u.ldo = d1;
@@ -335,10 +361,21 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
       {
         Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * n * d1 * (double)(a1 + 2 * a2));
         TcGemmArgs m{};
-        bool ok = tc_segment(m, 0, c->wb_hi + c->wb_a[l], two ? c->wb_lo + c->wb_a[l] : nullptr, d1, c->ld_a[l],
-                             Hcb[0], Hcb[1], rows, ldc_b, tl);
-        ok = ok && tc_segment(m, 1, c->wb_hi + c->wb_de[l], two ? c->wb_lo + c->wb_de[l] : nullptr, d1,
-                              c->ld_de[l], M2b[0], M2b[1], rows, l2, tl);
+        const bool rm = !tangent && d1 % 8 == 0;
+        int ntf = 1;
+        const int tf = rm ? feature_tile(d1, &ntf) : 0;
+        bool ok;
+        if (rm) {
+          ok = tc_segment_rm(m, 0, Hcb[0], Hcb[1], rows, ldc_b, c->wb_hi + c->wb_a[l],
+                             two ? c->wb_lo + c->wb_a[l] : nullptr, d1, c->ld_a[l], tf);
+          ok = ok && tc_segment_rm(m, 1, M2b[0], M2b[1], rows, l2, c->wb_hi + c->wb_de[l],
+                                   two ? c->wb_lo + c->wb_de[l] : nullptr, d1, c->ld_de[l], tf);
+        } else {
+          ok = tc_segment(m, 0, c->wb_hi + c->wb_a[l], two ? c->wb_lo + c->wb_a[l] : nullptr, d1, c->ld_a[l],
+                          Hcb[0], Hcb[1], rows, ldc_b, tl);
+          ok = ok && tc_segment(m, 1, c->wb_hi + c->wb_de[l], two ? c->wb_lo + c->wb_de[l] : nullptr, d1,
+                                c->ld_de[l], M2b[0], M2b[1], rows, l2, tl);
+        }
         m.nseg = 2;
         m.terms = c->terms;
         m.seg_terms[0] = m.seg_terms[1] = c->terms;
@@ -357,9 +394,16 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         }
         m.rows = rows;
         m.mfeat = d1;
-        m.tile_n = tl;
-        m.n_tiles_n = (int)((rows + tl - 1) / tl);
-        m.n_tiles_m = (d1 + 127) / 128;
+        if (rm) {
+          m.rm = 1;
+          m.tile_n = tf;
+          m.n_tiles_n = ntf;
+          m.n_tiles_m = (int)((rows + 127) / 128);
+        } else {
+          m.tile_n = tl;
+          m.n_tiles_n = (int)((rows + tl - 1) / tl);
+          m.n_tiles_m = (d1 + 127) / 128;
+        }
         m.mode = tangent ? 1 : 2;
         m.bias = P + c->lay.b[l];
         m.bias_period = C;
@@ -390,17 +434,30 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
       const double same_spin = (double)t.n_up * t.n_up + (double)t.n_down * t.n_down;
       Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, 2.0 * (double)Bc * Creal * d1 * K * same_spin);
       TcGemmArgs o{};
-      const int to = plain_tile(rows);
-      bool ok = tc_segment(o, 0, c->wb_hi + c->wb_orb, two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb,
-                           Hcb[0], Hcb[1], rows, ldh, to);
+      const bool rm = Ktot % 4 == 0;
+      bool ok;
+      if (rm) {
+        int ntf = 1;
+        const int tf = feature_tile(Ktot, &ntf);
+        ok = tc_segment_rm(o, 0, Hcb[0], Hcb[1], rows, ldh, c->wb_hi + c->wb_orb,
+                           two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb, tf);
+        o.rm = 1;
+        o.tile_n = tf;
+        o.n_tiles_n = ntf;
+        o.n_tiles_m = (int)((rows + 127) / 128);
+      } else {
+        const int to = plain_tile(rows);
+        ok = tc_segment(o, 0, c->wb_hi + c->wb_orb, two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb, Hcb[0],
+                        Hcb[1], rows, ldh, to);
+        o.tile_n = to;
+        o.n_tiles_n = (int)((rows + to - 1) / to);
+        o.n_tiles_m = (int)((Ktot + 127) / 128);
+      }
       o.nseg = 1;
       o.terms = c->terms;
       o.seg_terms[0] = c->terms;
       o.rows = rows;
       o.mfeat = (int)Ktot;
-      o.tile_n = to;
-      o.n_tiles_n = (int)((rows + to - 1) / to);
-      o.n_tiles_m = (int)((Ktot + 127) / 128);
       o.mode = 0;
       o.out = O;
       o.ldo = Ktot;

@@ -298,6 +298,8 @@ struct TangentSmem {
   T Eg[3][NM][NM + 1];
   T El[NM][NM + 1];
   T Xs[128 * NM];
+  T Tr[128];   // [cb][ns] diagonal entries of X_c
+  T Tr2[128];  // [cb][ns] row i of X_c times column i of X_c
 };
 
 // Tangent-pass body for one matrix in precision T (128 threads).  Returns
@@ -403,12 +405,22 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
       }
     }
     __syncthreads();
+    // traces, one thread per (coordinate, row i): row i of X_c against column
+    // i, then a reduction over i inside each coordinate's group of threads
+    if (cl < cb && c < n3) {
+      const T* X = sm.Xs + (long)cl * ns * ns;
+      const int i = j;  // thread (cl, j) takes row i = j
+      T r2 = T(0);
+      for (int j2 = 0; j2 < ns; ++j2) r2 = fma(X[i * ns + j2], X[j2 * ns + i], r2);
+      sm.Tr[cl * ns + i] = X[i * ns + i];  // index = thread id < cb * ns <= 128
+      sm.Tr2[cl * ns + i] = r2;
+    }
+    __syncthreads();
     if (tid < cb && c0 + tid < n3) {
-      const T* X = sm.Xs + (long)tid * ns * ns;
       T tr = T(0), tr2 = T(0);
       for (int i = 0; i < ns; ++i) {
-        tr += X[i * ns + i];
-        for (int j2 = 0; j2 < ns; ++j2) tr2 = fma(X[i * ns + j2], X[j2 * ns + i], tr2);
+        tr += sm.Tr[tid * ns + i];
+        tr2 += sm.Tr2[tid * ns + i];
       }
       a.dgrad[mat * n3 + c0 + tid] = (float)tr;
       part -= (double)tr2;

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_mean2_rows(const float* __restrict__ E,
                                                     __nv_bfloat16* __restrict__ lo, int ldb) {
   extern __shared__ float sh[];
   float* Es = sh;                              // [n][Q][din2]
-  float* Ss = sh + MAXN * kQ * 32;             // [2][Q][din2] per-spin sums
+  float* Ss = sh + n * Q * din2;               // [2][Q][din2] per-spin sums
   const long wi = blockIdx.x;
   const int i = (int)(wi % n);
   const int QD = Q * din2;
@@ -301,16 +301,18 @@ void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int 
 
 void launch_mean2(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C, float* M2) {
   if (Bc * n <= 0) return;
-  const size_t smem = sizeof(float) * (64 * kQ * 32 + 2 * kQ * 32);
-  FN_COUNT(1), k_mean2_rows<64><<<(unsigned)(Bc * n), 256, smem, s>>>(E, n, n_up, Q, din2, C, M2, nullptr, nullptr,
-                                                                      2 * din2);
+  const size_t smem = sizeof(float) * ((size_t)(n + 2) * Q * din2);
+  const int bs = C * 2 * din2 >= 1024 ? 256 : 64;
+  FN_COUNT(1), k_mean2_rows<64><<<(unsigned)(Bc * n), bs, smem, s>>>(E, n, n_up, Q, din2, C, M2, nullptr, nullptr,
+                                                                     2 * din2);
 }
 
 void launch_mean2_bf16(cudaStream_t s, const float* E, long Bc, int n, int n_up, int Q, int din2, int C,
                        __nv_bfloat16* hi, __nv_bfloat16* lo, long ldb) {
   if (Bc * n <= 0) return;
-  const size_t smem = sizeof(float) * (64 * kQ * 32 + 2 * kQ * 32);
-  FN_COUNT(1), k_mean2_rows<64><<<(unsigned)(Bc * n), 256, smem, s>>>(E, n, n_up, Q, din2, C, nullptr, hi, lo, (int)ldb);
+  const size_t smem = sizeof(float) * ((size_t)(n + 2) * Q * din2);
+  const int bs = C * ldb >= 1024 ? 256 : 64;
+  FN_COUNT(1), k_mean2_rows<64><<<(unsigned)(Bc * n), bs, smem, s>>>(E, n, n_up, Q, din2, C, nullptr, hi, lo, (int)ldb);
 }
 
 void launch_mean1_bf16(cudaStream_t s, const __nv_bfloat16* hi, const __nv_bfloat16* lo, long ldin, long Bc, int n,

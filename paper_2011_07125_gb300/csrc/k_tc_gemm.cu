@@ -298,24 +298,106 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       const bool fok = f < a.mfeat;
       const uint32_t tbase = tmem_base + ((uint32_t)lane_base << 16) + (uint32_t)(acc * 256);
       const long r_tile = (long)tn * tile_n;
-      if (a.mode == 2) {
-        // value pass: h = tanh(acc + U[walker] + b) (+ residual), one column per row
+      if (a.rm) {
+        // rows on TMEM lanes: this thread owns row r and reads 8 features per
+        // tcgen05.ld; loads and stores are 16-byte vectors along the features
+        const long r = (long)tm * BM + lane_base + lane;
+        const bool rok = r < a.rows;
+        const int ldb = (int)a.ldhb;
+        const float* __restrict__ urow = (a.mode == 2 && rok) ? Up + (r / a.u_div) * a.ldu : nullptr;
+        for (int f0 = half * 8; f0 < tile_n; f0 += 16) {
+          const int fb = tn * tile_n + f0;
+          if (fb >= a.mfeat) break;  // warp-uniform
+          float v[8];
+          tmem_ld8(tbase + f0, v);
+          if (!rok) continue;
+          const bool full8 = fb + 8 <= a.mfeat;
+          if (a.mode == 0) {
+            const bool brow = bias && (r % a.bias_period) == 0;
+            float o[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[j] = v[j] + ((brow && fb + j < a.mfeat) ? bias[fb + j] : 0.f);
+            if (oh) {
+              if (full8) {
+                uint4 hv, lv;
+                __nv_bfloat16* hp = reinterpret_cast<__nv_bfloat16*>(&hv);
+                __nv_bfloat16* lp = reinterpret_cast<__nv_bfloat16*>(&lv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  hp[j] = __float2bfloat16_rn(o[j]);
+                  lp[j] = __float2bfloat16_rn(o[j] - __bfloat162float(hp[j]));
+                }
+                *reinterpret_cast<uint4*>(oh + r * ldb + fb) = hv;
+                if (ol) *reinterpret_cast<uint4*>(ol + r * ldb + fb) = lv;
+              } else {
+                for (int j = 0; j < 8 && fb + j < a.mfeat; ++j) {
+                  const __nv_bfloat16 h = __float2bfloat16_rn(o[j]);
+                  oh[r * ldb + fb + j] = h;
+                  if (ol) ol[r * ldb + fb + j] = __float2bfloat16_rn(o[j] - __bfloat162float(h));
+                }
+              }
+            } else {
+              float* dst = out + r * a.ldo + fb;
+              if (full8) {
+                reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
+                reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
+              } else {
+                for (int j = 0; j < 8 && fb + j < a.mfeat; ++j) dst[j] = o[j];
+              }
+            }
+          } else {
+            // mode 2, value pass: tanh(acc + U + b) + residual (features padded to 8)
+            const float4 u0 = reinterpret_cast<const float4*>(urow + fb)[0];
+            const float4 u1 = reinterpret_cast<const float4*>(urow + fb)[1];
+            const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            float res[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (rh) {
+              const uint4 hv = *reinterpret_cast<const uint4*>(rh + r * ldb + fb);
+              const __nv_bfloat16* hp = reinterpret_cast<const __nv_bfloat16*>(&hv);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) res[j] = __bfloat162float(hp[j]);
+              if (rl) {
+                const uint4 lv = *reinterpret_cast<const uint4*>(rl + r * ldb + fb);
+                const __nv_bfloat16* lp = reinterpret_cast<const __nv_bfloat16*>(&lv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) res[j] += __bfloat162float(lp[j]);
+              }
+            }
+            uint4 hv, lv;
+            __nv_bfloat16* hp = reinterpret_cast<__nv_bfloat16*>(&hv);
+            __nv_bfloat16* lp = reinterpret_cast<__nv_bfloat16*>(&lv);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float o = tanhf(v[j] + uu[j] + (bias ? bias[fb + j] : 0.f)) + res[j];
+              hp[j] = __float2bfloat16_rn(o);
+              lp[j] = __float2bfloat16_rn(o - __bfloat162float(hp[j]));
+            }
+            *reinterpret_cast<uint4*>(oh + r * ldb + fb) = hv;
+            if (ol) *reinterpret_cast<uint4*>(ol + r * ldb + fb) = lv;
+          }
+        }
+      } else if (a.mode == 2) {
+        // value pass: h = tanh(acc + U[walker] + b) (+ residual), one column per
+        // row; the next chunk's global loads are issued before the current one
+        // is processed
         const float bf = (fok && bias) ? bias[f] : 0.f;
         const int ldb = (int)a.ldhb;
-        for (int c0 = half * 8; c0 < tile_n; c0 += 16) {
-          const long rr = r_tile + c0;
-          if (rr >= a.rows) break;  // warp-uniform
-          float u8[8], r8[8];
+        auto load8 = [&](float (&u8)[8], float (&r8)[8], long rr) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const long r = rr + j;
             const bool ok = fok && r < a.rows;
             u8[j] = ok ? Up[(r / a.u_div) * a.ldu + f] : 0.f;
-            r8[j] = (ok && rh) ? __bfloat162float(rh[r * ldb + f]) : 0.f;
-            if (ok && rl) r8[j] += __bfloat162float(rl[r * ldb + f]);
+            float v = 0.f;
+            if (ok && rh) v += __bfloat162float(rh[r * ldb + f]);
+            if (ok && rl) v += __bfloat162float(rl[r * ldb + f]);
+            r8[j] = v;
           }
+        };
+        auto emit8 = [&](const float (&u8)[8], const float (&r8)[8], int c0) {
           float v[8];
           tmem_ld8(tbase + c0, v);
+          const long rr = r_tile + c0;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const long r = rr + j;
@@ -325,6 +407,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             oh[r * ldb + f] = h;
             if (ol) ol[r * ldb + f] = __float2bfloat16_rn(o - __bfloat162float(h));
           }
+        };
+        float ua[8], ra[8], ub[8], rbv[8];
+        int c0 = half * 8;
+        if (r_tile + c0 < a.rows) load8(ua, ra, r_tile + c0);
+        for (; c0 < tile_n; c0 += 32) {
+          if (r_tile + c0 >= a.rows) break;  // warp-uniform
+          const int c1 = c0 + 16;
+          const bool more = c1 < tile_n && r_tile + c1 < a.rows;
+          if (more) load8(ub, rbv, r_tile + c1);
+          emit8(ua, ra, c0);
+          if (!more) break;
+          const int c2 = c1 + 16;
+          if (c2 < tile_n && r_tile + c2 < a.rows) load8(ua, ra, r_tile + c2);
+          emit8(ub, rbv, c1);
         }
       } else if (a.mode == 0) {
         const float bf = (fok && bias) ? bias[f] : 0.f;
@@ -491,6 +587,9 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a) {
   });
   if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.nseg < 1 || a.nseg > 3 || a.mode < 0 || a.mode > 2)
     return FN_EINVAL;
+  if (a.rm && (a.mode == 1 || (a.mode == 2 && (a.mfeat % 8 || a.ldu % 4 || a.ldhb % 8)) ||
+               (a.mode == 0 && (a.hb_hi ? a.ldhb % 8 : a.ldo % 4))))
+    return FN_EINVAL;
   for (int sg = 0; sg < a.nseg; ++sg) {
     if (a.seg_terms[sg] < 1 || a.seg_terms[sg] > 3 || a.kblocks[sg] < 1) return FN_EINVAL;
     if (a.seg_group[sg] && (a.seg_group[sg] % 8 || a.tile_n % a.seg_group[sg] || a.u_div < 1)) return FN_EINVAL;
@@ -506,11 +605,21 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a) {
 }  // namespace fn
 
 extern "C" fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, float* d_C, int M, int N, int K,
-                                             int tile_n, void* stream, unsigned* d_status) {
+                                             int tile_n, int rows_on_lanes, void* stream, unsigned* d_status) {
   using namespace fn;
   if (!d_A || !d_B || !d_C || !d_status || M < 1 || N < 1 || K < 1 || K % BK) return FN_EINVAL;
   TcGemmArgs a{};
-  if (!tc_make_map(&a.A[0][0], d_A, M, K, BM) || !tc_make_map(&a.B[0][0], d_B, N, K, tile_n)) return FN_EINVAL;
+  if (rows_on_lanes) {
+    // rows of C (from B) on the MMA M dimension, columns of C (from A) on N
+    if (!tc_make_map(&a.A[0][0], d_B, N, K, BM) || !tc_make_map(&a.B[0][0], d_A, M, K, tile_n)) return FN_EINVAL;
+    a.rm = 1;
+    a.n_tiles_n = (M + tile_n - 1) / tile_n;
+    a.n_tiles_m = (N + BM - 1) / BM;
+  } else {
+    if (!tc_make_map(&a.A[0][0], d_A, M, K, BM) || !tc_make_map(&a.B[0][0], d_B, N, K, tile_n)) return FN_EINVAL;
+    a.n_tiles_n = (N + tile_n - 1) / tile_n;
+    a.n_tiles_m = (M + BM - 1) / BM;
+  }
   a.A[0][1] = a.A[0][0];
   a.B[0][1] = a.B[0][0];
   a.kblocks[0] = K / BK;
@@ -520,8 +629,6 @@ extern "C" fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, f
   a.rows = N;
   a.mfeat = M;
   a.tile_n = tile_n;
-  a.n_tiles_n = (N + tile_n - 1) / tile_n;
-  a.n_tiles_m = (M + BM - 1) / BM;
   a.mode = 0;
   a.out = d_C;
   a.ldo = M;

@@ -22,6 +22,9 @@ struct TcGemmArgs {
   int mfeat;              // output features (M dimension)
   int tile_n;             // rows per tile: multiple of 16, <= 256
   int n_tiles_n, n_tiles_m;
+  int rm;                 // 1: rows of the output on the MMA M dimension (TMEM lanes) and
+                          //    features on N: A = activations, B = weights, tile_n =
+                          //    features per tile (modes 0 and 2 only); 0: features on M
   int mode;               // 0: plain store; 1: fused forward-Laplacian tanh layer;
                           // 2: value-pass layer (tanh of acc + U + b, plus residual)
   // mode 0 (FP32 out, or BF16 hi/lo into hb_hi/hb_lo with ld ldhb when hb_hi is set)

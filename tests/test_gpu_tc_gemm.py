@@ -14,21 +14,23 @@ def _fn():
     lib = binding.load()
     f = lib.ferminet_diag_bf16_gemm
     vp = C.c_void_p
-    f.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
+    f.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     f.restype = C.c_int
     return f
 
 
+@pytest.mark.parametrize("rm", [0, 1])
 @pytest.mark.parametrize("M,N,K,tile_n", [(128, 256, 64, 256), (256, 1000, 256, 192), (480, 37, 128, 176),
-                                          (256, 4099, 320, 224), (96, 50, 64, 16), (512, 700, 512, 256)])
-def test_bf16_gemm_matches_torch(M, N, K, tile_n):
+                                          (256, 4099, 320, 224), (96, 50, 64, 16), (512, 700, 512, 256),
+                                          (480, 1500, 256, 240)])
+def test_bf16_gemm_matches_torch(M, N, K, tile_n, rm):
     f = _fn()
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
     Cm = torch.full((N, M), float("nan"), device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rc = f(A.data_ptr(), B.data_ptr(), Cm.data_ptr(), M, N, K, tile_n,
+    rc = f(A.data_ptr(), B.data_ptr(), Cm.data_ptr(), M, N, K, tile_n, rm,
            C.c_void_p(torch.cuda.current_stream().cuda_stream), st.data_ptr())
     assert rc == 0
     torch.cuda.synchronize()
