@@ -335,34 +335,48 @@ def run_gpu(args, wl):
         fp32 = {"value": wl.batch * n32 / (t32 * 1e-3), "unit": UNIT, "ms_per_step": t32 / n32}
         f32.close()
 
-    # end to end through the public API: host (pinned) walkers in, energy and gradient out, every step
+    # end to end through the public API (ferminet_step, replayed from its CUDA
+    # graph): walker state in from pinned host memory and walker state, local
+    # energies, energy means and gradient back to pinned host memory, every step
     xh = torch.from_numpy(x0).pin_memory()
+    lph = fn.logpsi(torch.from_numpy(x0).to(dev), with_sign=False).cpu().pin_memory()
     eh = torch.empty(wl.batch, dtype=torch.float32).pin_memory()
     gh = torch.empty(fn.n_params, dtype=torch.float32).pin_memory()
     mh = torch.empty(len(wl.geoms), dtype=torch.float64).pin_memory()
     xd = torch.empty_like(x)
+    lpd = torch.empty_like(lp)
+    outb = {"eloc": torch.empty(wl.batch, device=dev), "emean": torch.empty(len(wl.geoms), dtype=torch.float64,
+                                                                            device=dev),
+            "grad": torch.empty(fn.n_params, device=dev), "accepted": torch.empty(wl.batch, dtype=torch.int32,
+                                                                                  device=dev)}
     n_e2e = max(2, min(args.steps, 5))
+
+    def e2e_step(k):
+        xd.copy_(xh, non_blocking=True)
+        lpd.copy_(lph, non_blocking=True)
+        fn.step(xd, lpd, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, 10 ** 6 + k * wl.mcmc_steps,
+                use_graph=True, out=outb)
+        xh.copy_(xd, non_blocking=True)
+        lph.copy_(lpd, non_blocking=True)
+        eh.copy_(outb["eloc"], non_blocking=True)
+        gh.copy_(outb["grad"], non_blocking=True)
+        mh.copy_(outb["emean"], non_blocking=True)
+
+    e2e_step(-1)  # capture
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(s)
     for k in range(n_e2e):
-        xd.copy_(xh, non_blocking=True)
-        lpd = fn.logpsi(xd, with_sign=False)
-        fn.mcmc_step(xd, lpd, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, 10 ** 6 + k * wl.mcmc_steps)
-        o = fn.local_energy(xd)
-        em2, g2 = fn.energy_grad(xd, o["eloc"])
-        xh.copy_(xd, non_blocking=True)
-        eh.copy_(o["eloc"], non_blocking=True)
-        gh.copy_(g2, non_blocking=True)
-        mh.copy_(em2, non_blocking=True)
+        e2e_step(k)
     t1.record(s)
     torch.cuda.synchronize()
     e2e_ms = t0.elapsed_time(t1) / n_e2e
     e2e = {"value": world * wl.batch / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(xh.numel() * 4),
-           "d2h_bytes_per_step": int(xh.numel() * 4 + eh.numel() * 4 + gh.numel() * 4 + mh.numel() * 8),
-           "note": "includes one extra log|psi| pass per step for the uploaded walkers"}
+           "h2d_bytes_per_step": int(xh.numel() * 4 + lph.numel() * 4),
+           "d2h_bytes_per_step": int(xh.numel() * 4 + lph.numel() * 4 + eh.numel() * 4 + gh.numel() * 4 +
+                                     mh.numel() * 8),
+           "api": "ferminet_step (CUDA graph replay)"}
 
     cpu = None
     err = None

@@ -171,6 +171,20 @@ fn_status ferminet_energy_grad(fn_ctx* ctx, const float* d_x, long B, const floa
 fn_status ferminet_mcmc_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_steps, float width,
                              uint64_t seed, uint64_t counter, int* d_accepted);
 
+/* One whole VMC step over the batch (the path of Eq. 2 per optimisation
+ * iteration): n_steps Metropolis moves exactly as ferminet_mcmc_step (counter
+ * t = counter + s), then the local energy at the new positions (d_eloc [B]),
+ * then the VMC energy gradient (d_emean [n_geoms] double, d_grad [n_params]) as
+ * ferminet_energy_grad.  d_x and d_logpsi are updated in place; d_accepted may
+ * be NULL.  With use_graph != 0 the step's kernels are captured once into a
+ * CUDA graph (keyed by B, n_steps, width, seed and the buffer addresses) and
+ * replayed on later calls; the counter is passed through device memory, so a
+ * new counter does not re-capture.  Results are identical with and without the
+ * graph.  Per-class profiling does not see graph replays. */
+fn_status ferminet_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_steps, float width, uint64_t seed,
+                        uint64_t counter, float* d_eloc, double* d_emean, float* d_grad, int* d_accepted,
+                        int use_graph);
+
 /* Synchronises the context stream and reads the device status word:
  * FN_ESINGULAR / FN_ENONFINITE if any walker since the last sync had a
  * singular orbital matrix or a non-finite output, else FN_OK or a CUDA error.

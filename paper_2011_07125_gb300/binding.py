@@ -55,7 +55,7 @@ class FermiNetError(RuntimeError):
 
 EXPORTS = ("ferminet_init", "ferminet_param_layout", "ferminet_net_layout", "ferminet_set_params",
            "ferminet_logpsi", "ferminet_local_energy", "ferminet_logpsi_vjp", "ferminet_energy_grad",
-           "ferminet_mcmc_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
+           "ferminet_mcmc_step", "ferminet_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
            "ferminet_profile_read", "ferminet_launch_count", "ferminet_last_error", "ferminet_destroy")
 KERNEL_CLASSES = {"tangent_gemm": 0, "det_tangent": 1, "two_layer": 2, "means": 3, "tanh": 4, "value_pass": 5,
                   "adjoint": 6}
@@ -86,6 +86,8 @@ def load(path: Optional[str] = None):
         lib.ferminet_logpsi_vjp.argtypes = [vp, vp, C.c_long, vp, vp]
         lib.ferminet_energy_grad.argtypes = [vp, vp, C.c_long, vp, vp, vp]
         lib.ferminet_mcmc_step.argtypes = [vp, vp, vp, C.c_long, C.c_int, C.c_float, C.c_uint64, C.c_uint64, vp]
+        lib.ferminet_step.argtypes = [vp, vp, vp, C.c_long, C.c_int, C.c_float, C.c_uint64, C.c_uint64, vp, vp, vp,
+                                      vp, C.c_int]
         lib.ferminet_sync.argtypes = [vp]
         lib.ferminet_flagged_matrices.argtypes = [vp]
         lib.ferminet_flagged_matrices.restype = C.c_long
@@ -237,6 +239,20 @@ class FermiNet:
         self._check(self.lib.ferminet_mcmc_step(self.ctx, _ptr(x), _ptr(logpsi), B, int(n_steps), float(width),
                                                 int(seed), int(counter), _ptr(accepted)), "ferminet_mcmc_step")
         return accepted
+
+    def step(self, x, logpsi, n_steps, width, seed, counter, use_graph=True, out=None):
+        """One VMC step (Metropolis moves, local energy, VMC gradient); x and
+        logpsi are advanced in place.  Returns dict(eloc, emean, grad, accepted)."""
+        B = x.shape[0]
+        self._f32(x, (B, self.n, 3))
+        self._f32(logpsi, (B,))
+        if out is None:
+            out = {"eloc": self._empty(B), "emean": self._empty(self.G, dtype=self.torch.float64),
+                   "grad": self._empty(self.n_params), "accepted": self._empty(B, dtype=self.torch.int32)}
+        self._check(self.lib.ferminet_step(self.ctx, _ptr(x), _ptr(logpsi), B, int(n_steps), float(width), int(seed),
+                                           int(counter), _ptr(out["eloc"]), _ptr(out["emean"]), _ptr(out["grad"]),
+                                           _ptr(out["accepted"]), 1 if use_graph else 0), "ferminet_step")
+        return out
 
     def sync(self):
         rc = self.lib.ferminet_sync(self.ctx)

@@ -870,6 +870,46 @@ fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, c
 
 }  // namespace fn
 
+namespace {
+
+// The whole VMC step: n_steps Metropolis moves (counter = base + s, with the
+// base either `counter` or, when dctr is set, read from device memory), then
+// the local energy at the new positions, then the VMC energy gradient.
+fn_status run_step(fn_ctx* c, float* x, float* lp, long B, int n_steps, float width, uint64_t seed,
+                   uint64_t counter, const uint64_t* dctr, float* eloc, double* emean, float* grad, int* acc) {
+  const int n3 = 3 * c->n;
+  float* xp = c->aux;
+  float* lpp = c->aux + (size_t)B * n3;
+  float* seeds = c->aux;  // reused after the moves
+  if (acc) cudaMemsetAsync(acc, 0, sizeof(int) * B, c->stream);
+  for (int s = 0; s < n_steps; ++s) {
+    const uint64_t t = (dctr ? 0 : counter) + (uint64_t)s;
+    launch_propose(c->stream, x, xp, B, n3, width, seed, t, dctr);
+    fn_status st = run_passes(c, xp, B, false, FwdOut{lpp, nullptr, nullptr, nullptr});
+    if (st != FN_OK) return st;
+    launch_accept(c->stream, x, xp, lp, lpp, B, n3, seed, t, acc, dctr);
+  }
+  fn_status st = run_passes(c, x, B, true, FwdOut{nullptr, nullptr, eloc, nullptr});
+  if (st != FN_OK) return st;
+  const long B1 = c->G > 1 ? 0 : B;
+  launch_emean(c->stream, eloc, c->G, c->d_geo_off, c->d_geo_cnt, B1, emean);
+  launch_seeds(c->stream, eloc, B, c->G > 1 ? c->d_geo : nullptr, emean, c->d_geo_cnt, B1, seeds);
+  return run_vjp(c, x, B, seeds, grad);
+}
+
+// Workspace large enough for every pass of a step (so a captured step never
+// allocates).
+fn_status ensure_step_ws(fn_ctx* c, long B) {
+  size_t need = 0;
+  for (int mode = 0; mode < 3; ++mode) {
+    const long ch = chunk_for(c, B, mode);
+    need = std::max(need, ws_bytes(c, ch, mode));
+  }
+  return ensure_ws(c, need);
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1107,11 +1147,89 @@ fn_status ferminet_mcmc_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int
   if (d_accepted) CK(cudaMemsetAsync(d_accepted, 0, sizeof(int) * B, c->stream));
   for (int s = 0; s < n_steps; ++s) {
     const uint64_t tc = counter + (uint64_t)s;
-    launch_propose(c->stream, d_x, xp, B, n3, width, seed, tc);
+    launch_propose(c->stream, d_x, xp, B, n3, width, seed, tc, nullptr);
     st = run_passes(c, xp, B, false, FwdOut{lpp, nullptr, nullptr, nullptr});
     if (st != FN_OK) return st;
-    launch_accept(c->stream, d_x, xp, d_logpsi, lpp, B, n3, seed, tc, d_accepted);
+    launch_accept(c->stream, d_x, xp, d_logpsi, lpp, B, n3, seed, tc, d_accepted, nullptr);
   }
+  return after_launch(c);
+}
+
+fn_status ferminet_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_steps, float width, uint64_t seed,
+                        uint64_t counter, float* d_eloc, double* d_emean, float* d_grad, int* d_accepted,
+                        int use_graph) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (B < 1 || !d_logpsi || !d_eloc || !d_emean || !d_grad) return fail(c, FN_EINVAL, "null step buffer");
+  if (n_steps < 0 || !(width >= 0.f)) return fail(c, FN_EINVAL, "bad step count or width");
+  st = ensure_aux(c, B);
+  if (st != FN_OK) return st;
+  st = ensure_step_ws(c, B);
+  if (st != FN_OK) return st;
+  if (!use_graph)
+    return run_step(c, d_x, d_logpsi, B, n_steps, width, seed, counter, nullptr, d_eloc, d_emean, d_grad,
+                    d_accepted) == FN_OK
+               ? after_launch(c)
+               : FN_ECUDA;
+  if (!c->d_counter) CK(cudaMalloc(&c->d_counter, sizeof(uint64_t)));
+  if (!c->graph_stream) {
+    CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  }
+  cudaStream_t user = c->stream, gs = c->graph_stream;
+  CK(cudaEventRecord(c->ev_in, user));
+  CK(cudaStreamWaitEvent(gs, c->ev_in, 0));
+  fn_ctx::StepKey key;
+  memset(&key, 0, sizeof key);  // padding bytes take part in the comparison
+  key.B = B;
+  key.n_steps = n_steps;
+  key.width = width;
+  key.seed = seed;
+  key.x = d_x;
+  key.lp = d_logpsi;
+  key.eloc = d_eloc;
+  key.emean = d_emean;
+  key.grad = d_grad;
+  key.acc = d_accepted;
+  key.ws = c->ws;
+  key.aux = c->aux;
+  key.ws_size = c->ws_size;
+  const bool same = c->step_exec && memcmp(&key, &c->step_key, sizeof key) == 0;
+  launch_set_u64(gs, c->d_counter, counter);
+  if (!same) {
+    if (c->step_exec) {
+      cudaGraphExecDestroy(c->step_exec);
+      c->step_exec = nullptr;
+    }
+    const bool prof = c->prof_on;
+    c->prof_on = false;  // no event records inside the captured graph
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    c->stream = gs;
+    fn_status rs = run_step(c, d_x, d_logpsi, B, n_steps, width, seed, 0, c->d_counter, d_eloc, d_emean, d_grad,
+                            d_accepted);
+    c->stream = user;
+    cudaError_t ce = cudaStreamEndCapture(gs, &graph);
+    c->prof_on = prof;
+    if (rs != FN_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(c, FN_ECUDA, "step capture failed");
+    }
+    cudaError_t ie = cudaGraphInstantiate(&c->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      c->step_exec = nullptr;
+      cudaGetLastError();
+      return fail(c, FN_ECUDA, "step graph instantiation failed");
+    }
+    c->step_key = key;
+  }
+  CK(cudaGraphLaunch(c->step_exec, gs));
+  CK(cudaEventRecord(c->ev_out, gs));
+  CK(cudaStreamWaitEvent(user, c->ev_out, 0));
   return after_launch(c);
 }
 
@@ -1179,6 +1297,14 @@ void ferminet_destroy(fn_ctx* c) {
   cudaFree(c->wb_hi);
   cudaFree(c->wb_lo);
   cudaFree(c->ident);
+  cudaFree(c->d_counter);
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->graph_stream) {
+    cudaStreamSynchronize(c->graph_stream);
+    cudaStreamDestroy(c->graph_stream);
+  }
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   drain_profile(c);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;

@@ -128,10 +128,12 @@ void launch_det(cudaStream_t s, const DetArgs& a);
 void launch_combine(cudaStream_t s, const float* logdet, const float* sign, const float* dgrad, const float* dlap,
                     const float* x, long Bc, long w0, int n, int K, int N, Geo g, bool tangent, float* logpsi,
                     float* psign, float* eloc, float* kinetic, float* wdet, unsigned* status);
+// Metropolis kernels; with dctr non-null the counter is t + *dctr (device memory).
 void launch_propose(cudaStream_t s, const float* x, float* xp, long B, int n3, float width, uint64_t seed,
-                    uint64_t t);
+                    uint64_t t, const uint64_t* dctr);
 void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, const float* lp_prop, long B, int n3,
-                   uint64_t seed, uint64_t t, int* accepted);
+                   uint64_t seed, uint64_t t, int* accepted, const uint64_t* dctr);
+void launch_set_u64(cudaStream_t s, uint64_t* p, uint64_t v);
 // With G == 1 the single geometry holds all B walkers (B1 = B); otherwise the
 // device tables d_off / d_cnt give each geometry's walker range.
 void launch_emean(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
@@ -213,6 +215,19 @@ struct fn_ctx {
   long wb_total = 0;
   __nv_bfloat16* ident = nullptr;  // 128 x 128 BF16 identity (operand of the folded per-walker term)
   int force64 = 0;
+  // captured full step (ferminet_step with use_graph)
+  uint64_t* d_counter = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  cudaStream_t graph_stream = nullptr;  // captures and replays (the legacy default stream cannot capture)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  struct StepKey {
+    long B;
+    int n_steps;
+    float width;
+    uint64_t seed;
+    const void *x, *lp, *eloc, *emean, *grad, *acc, *ws, *aux;
+    size_t ws_size;
+  } step_key{};
   // per-class event timing
   bool prof_on = false;
   struct Pending {

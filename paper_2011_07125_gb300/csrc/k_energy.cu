@@ -143,7 +143,8 @@ __device__ __forceinline__ void box_muller(unsigned a, unsigned b, float& z0, fl
 }
 
 __global__ void k_propose(const float* __restrict__ x, float* __restrict__ xp, long B, int n3, float width,
-                          uint64_t seed, uint64_t t) {
+                          uint64_t seed, uint64_t t, const uint64_t* __restrict__ dctr) {
+  if (dctr) t += *dctr;  // graph replays read the step's base counter from device memory
   const int nb = (n3 + 3) / 4;
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= B * nb) return;
@@ -162,7 +163,9 @@ __global__ void k_propose(const float* __restrict__ x, float* __restrict__ xp, l
 }
 
 __global__ void k_accept(float* __restrict__ x, const float* __restrict__ xp, float* __restrict__ logpsi,
-                         const float* __restrict__ lpp, long B, int n3, uint64_t seed, uint64_t t, int* accepted) {
+                         const float* __restrict__ lpp, long B, int n3, uint64_t seed, uint64_t t, int* accepted,
+                         const uint64_t* __restrict__ dctr) {
+  if (dctr) t += *dctr;
   long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= B) return;
   uint4 o = philox10(make_uint4((unsigned)w, 0xFFFFFFFFu, (unsigned)t, (unsigned)(t >> 32)),
@@ -228,15 +231,20 @@ void launch_combine(cudaStream_t s, const float* logdet, const float* sign, cons
 }
 
 void launch_propose(cudaStream_t s, const float* x, float* xp, long B, int n3, float width, uint64_t seed,
-                    uint64_t t) {
+                    uint64_t t, const uint64_t* dctr) {
   long tot = B * ((n3 + 3) / 4);
-  if (tot > 0) FN_COUNT(1), k_propose<<<nblk(tot, 256), 256, 0, s>>>(x, xp, B, n3, width, seed, t);
+  if (tot > 0) FN_COUNT(1), k_propose<<<nblk(tot, 256), 256, 0, s>>>(x, xp, B, n3, width, seed, t, dctr);
 }
 
 void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, const float* lp_prop, long B, int n3,
-                   uint64_t seed, uint64_t t, int* accepted) {
-  if (B > 0) FN_COUNT(1), k_accept<<<nblk(B, 256), 256, 0, s>>>(x, xp, logpsi, lp_prop, B, n3, seed, t, accepted);
+                   uint64_t seed, uint64_t t, int* accepted, const uint64_t* dctr) {
+  if (B > 0)
+    FN_COUNT(1), k_accept<<<nblk(B, 256), 256, 0, s>>>(x, xp, logpsi, lp_prop, B, n3, seed, t, accepted, dctr);
 }
+
+__global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
+
+void launch_set_u64(cudaStream_t s, uint64_t* p, uint64_t v) { FN_COUNT(1), k_set_u64<<<1, 1, 0, s>>>(p, v); }
 
 void launch_emean(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
                   double* emean) {

@@ -206,3 +206,26 @@ def test_singular_walker_reported():
     assert st == "FN_ESINGULAR"
     assert np.isneginf(lp[1]) and sg.cpu().numpy()[1] == 0
     assert np.all(np.isfinite(lp[[0, 2, 3]]))
+
+
+@pytest.mark.parametrize("name,per,prec", [("ne", 32, "fp32"), ("c4h4x8", 4, "mixed")])
+def test_step_graph_matches_calls(name, per, prec):
+    """ferminet_step replayed from its CUDA graph (two steps, new counter each)
+    equals the same step issued as separate calls, bit for bit."""
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P, prec)
+    xa = cuda(x)
+    xb = cuda(x)
+    la = fn.logpsi(xa, with_sign=False)
+    lb = la.clone()
+    for k in range(2):
+        ctr = 100 + 7 * k
+        acc = fn.mcmc_step(xa, la, 3, 0.1, 9, ctr)
+        e = fn.local_energy(xa)["eloc"]
+        em, g = fn.energy_grad(xa, e)
+        o = fn.step(xb, lb, 3, 0.1, 9, ctr, use_graph=True)
+        assert fn.sync() == "FN_OK"
+        assert torch.equal(xa, xb) and torch.equal(la, lb)
+        assert torch.equal(acc, o["accepted"])
+        assert torch.equal(e, o["eloc"]) and torch.equal(em, o["emean"])
+        assert torch.equal(g, o["grad"])
