@@ -7,14 +7,72 @@
 namespace fn {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
+constexpr int BM = 128, BN = 128, BK = 16, NT = 256;
+
+// One 8-element run of a 128 x 16 operand tile per thread: along k when the
+// operand is K-contiguous (row = t / 2, k offset 8 (t % 2)), along m/n
+// otherwise (k = t / 16, offset 8 (t % 16)).  float4 loads when the run is in
+// bounds and the row stride allows it.
+template <bool KM>
+__device__ __forceinline__ void load_run(const float* __restrict__ P, long ld, long r0, long R, long k0, long k1,
+                                         int tid, bool vec, float (&v)[8]) {
+  if (KM) {
+    const long r = r0 + (tid >> 1);
+    const long k = k0 + (tid & 1) * 8;
+    if (r < R) {
+      const float* p = P + r * ld + k;
+      if (vec && k + 8 <= k1) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        const float4 b = reinterpret_cast<const float4*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        return;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (k + q < k1) ? p[q] : 0.f;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = 0.f;
+    }
+  } else {
+    const long k = k0 + (tid >> 4);
+    const long r = r0 + (tid & 15) * 8;
+    if (k < k1) {
+      const float* p = P + k * ld + r;
+      if (vec && r + 8 <= R) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        const float4 b = reinterpret_cast<const float4*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        return;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (r + q < R) ? p[q] : 0.f;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = 0.f;
+    }
+  }
+}
+
+template <bool KM>
+__device__ __forceinline__ void store_run(float (*S)[BM], int tid, const float (&v)[8]) {
+  if (KM) {
+    const int r = tid >> 1, k = (tid & 1) * 8;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) S[k + q][r] = v[q];
+  } else {
+    const int k = tid >> 4, r = (tid & 15) * 8;
+    reinterpret_cast<float4*>(&S[k][r])[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(&S[k][r])[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
 
 // A_KM: A stored [M][K] (k contiguous) else [K][M].
 // B_KM: B stored [N][K] (k contiguous) else [K][N].
 template <bool A_KM, bool B_KM>
-__global__ void __launch_bounds__(NT) k_sgemm(long M, long N, long K, const float* __restrict__ A, long lda,
+__global__ void __launch_bounds__(NT, 2) k_sgemm(long M, long N, long K, const float* __restrict__ A, long lda,
                                               const float* __restrict__ B, long ldb, float* __restrict__ Cm,
-                                              long ldc, Epi e, long k_per_split, int partial) {
+                                              long ldc, Epi e, long k_per_split, int partial, int vec_a,
+                                              int vec_b) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int tid = threadIdx.x;
@@ -23,50 +81,7 @@ __global__ void __launch_bounds__(NT) k_sgemm(long M, long N, long K, const floa
   const long kz1 = min(K, kz0 + k_per_split);
   if (partial) Cm += (long)blockIdx.z * M * ldc;
 
-  float ra[4], rb[4];
-  auto load = [&](long k0) {
-    if (A_KM) {
-      long m = m0 + (tid >> 1);
-      long k = k0 + (tid & 1) * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ra[q] = (m < M && k + q < kz1) ? A[m * lda + k + q] : 0.f;
-    } else {
-      long k = k0 + (tid >> 5);
-      long m = m0 + (tid & 31) * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ra[q] = (k < kz1 && m + q < M) ? A[k * lda + m + q] : 0.f;
-    }
-    if (B_KM) {
-      long nn = n0 + (tid >> 1);
-      long k = k0 + (tid & 1) * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) rb[q] = (nn < N && k + q < kz1) ? B[nn * ldb + k + q] : 0.f;
-    } else {
-      long k = k0 + (tid >> 5);
-      long nn = n0 + (tid & 31) * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) rb[q] = (k < kz1 && nn + q < N) ? B[k * ldb + nn + q] : 0.f;
-    }
-  };
-  auto store = [&](int buf) {
-    if (A_KM) {
-      int m = tid >> 1, k = (tid & 1) * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) As[buf][k + q][m] = ra[q];
-    } else {
-      int k = tid >> 5, m = (tid & 31) * 4;
-      *reinterpret_cast<float4*>(&As[buf][k][m]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
-    }
-    if (B_KM) {
-      int nn = tid >> 1, k = (tid & 1) * 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) Bs[buf][k + q][nn] = rb[q];
-    } else {
-      int k = tid >> 5, nn = (tid & 31) * 4;
-      *reinterpret_cast<float4*>(&Bs[buf][k][nn]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-    }
-  };
-
+  float ra[8], rb[8];
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -76,14 +91,19 @@ __global__ void __launch_bounds__(NT) k_sgemm(long M, long N, long K, const floa
   const int ty = tid >> 4, tx = tid & 15;
   long kt = kz0;
   if (kt < kz1) {
-    load(kt);
-    store(0);
+    load_run<A_KM>(A, lda, m0, M, kt, kz1, tid, vec_a, ra);
+    load_run<B_KM>(B, ldb, n0, N, kt, kz1, tid, vec_b, rb);
+    store_run<A_KM>(As[0], tid, ra);
+    store_run<B_KM>(Bs[0], tid, rb);
   }
   __syncthreads();
   int buf = 0;
   for (; kt < kz1; kt += BK) {
     const bool more = kt + BK < kz1;
-    if (more) load(kt + BK);
+    if (more) {
+      load_run<A_KM>(A, lda, m0, M, kt + BK, kz1, tid, vec_a, ra);
+      load_run<B_KM>(B, ldb, n0, N, kt + BK, kz1, tid, vec_b, rb);
+    }
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
@@ -97,7 +117,10 @@ __global__ void __launch_bounds__(NT) k_sgemm(long M, long N, long K, const floa
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (more) store(buf ^ 1);
+    if (more) {
+      store_run<A_KM>(As[buf ^ 1], tid, ra);
+      store_run<B_KM>(Bs[buf ^ 1], tid, rb);
+    }
     __syncthreads();
     buf ^= 1;
   }
@@ -137,10 +160,11 @@ template <bool A_KM, bool B_KM>
 void run(cudaStream_t s, long M, long N, long K, const float* A, long lda, const float* B, long ldb, float* C,
          long ldc, const Epi& e, long kps, int splits, int partial) {
   if (M <= 0 || N <= 0) return;
+  const int va = (lda % 4 == 0) && ((uintptr_t)A % 16 == 0);
+  const int vb = (ldb % 4 == 0) && ((uintptr_t)B % 16 == 0);
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
-  FN_COUNT(1), k_sgemm<A_KM, B_KM><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, e, kps, partial);
+  FN_COUNT(1), k_sgemm<A_KM, B_KM><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, e, kps, partial, va, vb);
 }
-
 }  // namespace
 
 void gemm_nt(cudaStream_t s, long M, long N, long K, const float* A, long lda, const float* B, long ldb, float* C,
@@ -155,11 +179,11 @@ void gemm_nn(cudaStream_t s, long M, long N, long K, const float* A, long lda, c
 
 int gemm_tn_splits(long M, long N, long K) {
   long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  long want = (2 * 152 + tiles - 1) / tiles;  // about two waves of CTAs
-  long maxs = (K + 255) / 256;                 // at least 256 rows per split
+  long want = (4 * 152 + tiles - 1) / tiles;  // about two waves of two CTAs per SM
+  long maxs = (K + 511) / 512;                 // at least 512 rows per split
   long sp = want < maxs ? want : maxs;
   if (sp < 1) sp = 1;
-  if (sp > 64) sp = 64;
+  if (sp > 1024) sp = 1024;
   return (int)sp;
 }
 
