@@ -255,6 +255,10 @@ def run_gpu(args, wl):
     fn.set_params(params)
     x = torch.from_numpy(x0).to(dev)
     lp = fn.logpsi(x, with_sign=False)
+    tuning = None
+    if prec == "mixed" and not args.no_autotune:
+        tuning, cached = fn.autotune_cached(x)
+        tuning = dict(tuning, cached=cached)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     counter = [0]
 
@@ -407,7 +411,7 @@ def run_gpu(args, wl):
                 "data": "synthetic (seeded walkers, N(0,1/fan_in) weights; the paper ships no data)",
                 "config": {"workload": describe(wl), "walkers": wl.batch, "precision": prec,
                            "l2": "256 MiB buffer written between timed steps, outside the timed events",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU", "tuning": tuning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "status": st, "fp32_path": fp32, "error_vs_oracle": err,
                 "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in classes.items()}}
@@ -427,6 +431,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "mixed"])
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     from paper_2011_07125_gb300 import synth
     wl = synth.workload(args.workload)

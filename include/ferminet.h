@@ -185,6 +185,31 @@ fn_status ferminet_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_
                         uint64_t counter, float* d_eloc, double* d_emean, float* d_grad, int* d_accepted,
                         int use_graph);
 
+/* Tile shapes of the tensor-core local-energy pass and the walker chunk.
+ * 0 in a field means the built-in default.
+ *   layer_groups:  (walker, electron) groups per tile of the fused layer GEMM
+ *                  (tile width = layer_groups * columns per group, <= 256 and a
+ *                  multiple of 16);
+ *   feature_tile:  features per tile of the rows-on-lanes GEMMs (orbitals and
+ *                  per-walker terms; a multiple of 16, <= 256);
+ *   tangent_chunk: walkers per local-energy chunk (bounded by the workspace
+ *                  budget). */
+typedef struct {
+  int layer_groups;
+  int feature_tile;
+  long tangent_chunk;
+} fn_tuning;
+
+fn_status ferminet_get_tuning(const fn_ctx* ctx, fn_tuning* out);
+/* Invalid fields (shapes the kernels cannot run) are rejected with FN_EINVAL. */
+fn_status ferminet_set_tuning(fn_ctx* ctx, const fn_tuning* t);
+
+/* Autotuner: times the local-energy pass on d_x [B][n][3] (repeats times per
+ * candidate, minimum kept) for every candidate combination of the three
+ * fields, installs the fastest in the context and returns it in *best (may be
+ * NULL).  Synchronises the stream.  Only meaningful in FN_PREC_MIXED. */
+fn_status ferminet_autotune(fn_ctx* ctx, const float* d_x, long B, int repeats, fn_tuning* best);
+
 /* Synchronises the context stream and reads the device status word:
  * FN_ESINGULAR / FN_ENONFINITE if any walker since the last sync had a
  * singular orbital matrix or a non-finite output, else FN_OK or a CUDA error.

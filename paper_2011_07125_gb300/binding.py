@@ -35,6 +35,10 @@ class FnGeometry(C.Structure):
                 ("walker_offset", C.c_long), ("walker_count", C.c_long)]
 
 
+class FnTuning(C.Structure):
+    _fields_ = [("layer_groups", C.c_int), ("feature_tile", C.c_int), ("tangent_chunk", C.c_long)]
+
+
 class FnParamEntry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("offset", C.c_long), ("count", C.c_long),
                 ("fan_in", C.c_long), ("kind", C.c_int), ("pad", C.c_int)]
@@ -56,7 +60,8 @@ class FermiNetError(RuntimeError):
 EXPORTS = ("ferminet_init", "ferminet_param_layout", "ferminet_net_layout", "ferminet_set_params",
            "ferminet_logpsi", "ferminet_local_energy", "ferminet_logpsi_vjp", "ferminet_energy_grad",
            "ferminet_mcmc_step", "ferminet_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
-           "ferminet_profile_read", "ferminet_launch_count", "ferminet_last_error", "ferminet_destroy")
+           "ferminet_profile_read", "ferminet_launch_count", "ferminet_get_tuning", "ferminet_set_tuning",
+           "ferminet_autotune", "ferminet_last_error", "ferminet_destroy")
 KERNEL_CLASSES = {"tangent_gemm": 0, "det_tangent": 1, "two_layer": 2, "means": 3, "tanh": 4, "value_pass": 5,
                   "adjoint": 6}
 
@@ -98,6 +103,9 @@ def load(path: Optional[str] = None):
         lib.ferminet_profile.argtypes = [vp, C.c_int]
         lib.ferminet_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long),
                                               C.POINTER(C.c_double)]
+        lib.ferminet_get_tuning.argtypes = [vp, C.POINTER(FnTuning)]
+        lib.ferminet_set_tuning.argtypes = [vp, C.POINTER(FnTuning)]
+        lib.ferminet_autotune.argtypes = [vp, vp, C.c_long, C.c_int, C.POINTER(FnTuning)]
         lib.ferminet_launch_count.argtypes = []
         lib.ferminet_launch_count.restype = C.c_longlong
         for f in EXPORTS:
@@ -155,6 +163,7 @@ class FermiNet:
             garr[i].walker_count = int(counts[i])
             off += int(counts[i])
         self.total = off
+        self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = C.c_void_p()
         fnet = _net(net)
@@ -268,6 +277,52 @@ class FermiNet:
         self._check(self.lib.ferminet_profile_read(self.ctx, KERNEL_CLASSES[name], C.byref(ms), C.byref(n),
                                                    C.byref(fl)), "ferminet_profile_read")
         return {"ms": ms.value, "launches": n.value, "alg_flops": fl.value}
+
+    def get_tuning(self):
+        t = FnTuning()
+        self._check(self.lib.ferminet_get_tuning(self.ctx, C.byref(t)), "ferminet_get_tuning")
+        return {"layer_groups": t.layer_groups, "feature_tile": t.feature_tile, "tangent_chunk": t.tangent_chunk}
+
+    def set_tuning(self, layer_groups=0, feature_tile=0, tangent_chunk=0):
+        t = FnTuning(int(layer_groups), int(feature_tile), int(tangent_chunk))
+        self._check(self.lib.ferminet_set_tuning(self.ctx, C.byref(t)), "ferminet_set_tuning")
+
+    def autotune(self, x, repeats=2):
+        """Times the candidate tile shapes on these walkers and installs the fastest."""
+        B = x.shape[0]
+        self._f32(x, (B, self.n, 3))
+        t = FnTuning()
+        self._check(self.lib.ferminet_autotune(self.ctx, _ptr(x), B, int(repeats), C.byref(t)), "ferminet_autotune")
+        return {"layer_groups": t.layer_groups, "feature_tile": t.feature_tile, "tangent_chunk": t.tangent_chunk}
+
+    def autotune_cached(self, x, cache_path=None, repeats=2):
+        """Tuning from a JSON cache keyed by network shape, batch, precision and
+        GPU; runs the autotuner and records the result on a miss."""
+        import json
+        torch = self.torch
+        path = cache_path or os.path.join(_HERE, "_build", "autotune.json")
+        key = "|".join(str(v) for v in (self.net.n_layers, self.net.d1, self.net.d2, self.net.n_det, self.net.n_up,
+                                         self.net.n_down, self.net.n_nuc, self.G, x.shape[0], self.precision,
+                                         torch.cuda.get_device_name()))
+        cache = {}
+        if os.path.exists(path):
+            try:
+                cache = json.load(open(path))
+            except Exception:
+                cache = {}
+        if key in cache:
+            self.set_tuning(**cache[key])
+            return cache[key], True
+        best = self.autotune(x, repeats)
+        cache[key] = best
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path + ".tmp", "w") as fh:
+                json.dump(cache, fh, indent=1)
+            os.replace(path + ".tmp", path)
+        except OSError:
+            pass
+        return best, False
 
     def flagged_matrices(self):
         return int(self.lib.ferminet_flagged_matrices(self.ctx))

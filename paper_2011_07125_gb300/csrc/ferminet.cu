@@ -190,9 +190,10 @@ bool tc_segment_rm(TcGemmArgs& g, int seg, const __nv_bfloat16* x_hi, const __nv
   return ok;
 }
 
-// Features per tile in the rows-on-lanes orientation (<= 256, multiple of 16).
-int feature_tile(long mfeat, int* n_tiles) {
-  const long nt = (mfeat + 255) / 256;
+// Features per tile in the rows-on-lanes orientation (<= cap, multiple of 16).
+int feature_tile(long mfeat, int* n_tiles, int cap = 256) {
+  if (cap < 16 || cap > 256 || cap % 16) cap = 256;
+  const long nt = (mfeat + cap - 1) / cap;
   const long per = (mfeat + nt - 1) / nt;
   *n_tiles = (int)nt;
   return (int)(((per + 15) / 16) * 16);
@@ -200,7 +201,8 @@ int feature_tile(long mfeat, int* n_tiles) {
 
 // Rows per tile of the fused layer epilogue: whole (walker, electron) groups of
 // C columns, at most 256 rows, a multiple of 16.
-int layer_tile(int C) {
+int layer_tile(int C, int groups = 0) {
+  if (groups > 0 && groups * C <= 256 && (groups * C) % 16 == 0) return groups * C;
   for (int g = 256 / C; g >= 1; --g)
     if ((g * C) % 16 == 0) return g * C;
   return 0;
@@ -308,7 +310,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     launch_split_bf16(s, H0, 4 * N, rows, 4 * N, H0b[0], H0b[1], ldh0);
     const __nv_bfloat16* Hcb[2] = {H0b[0], H0b[1]};
     long ldc_b = ldh0;
-    const int tl = tangent ? layer_tile(C) : plain_tile(rows);
+    const int tl = tangent ? layer_tile(C, c->tune.layer_groups) : plain_tile(rows);
     if (ldh != d1) {  // padding columns must read as zeros in the MMAs
       for (int h = 0; h < (two ? 2 : 1); ++h) {
         cudaMemsetAsync(Hab[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
@@ -333,7 +335,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * d1 * 2.0 * a1);
         TcGemmArgs u{};
         int ntf = 1;
-        const int tu = feature_tile(d1, &ntf);
+        const int tu = feature_tile(d1, &ntf, c->tune.feature_tile);
         bool ok = tc_segment_rm(u, 0, M1b[0], M1b[1], Bc * C, l1, c->wb_hi + c->wb_bc[l],
                                 two ? c->wb_lo + c->wb_bc[l] : nullptr, d1, c->ld_bc[l], tu);
         u.rm = 1;
@@ -363,7 +365,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         TcGemmArgs m{};
         const bool rm = !tangent && d1 % 8 == 0;
         int ntf = 1;
-        const int tf = rm ? feature_tile(d1, &ntf) : 0;
+        const int tf = rm ? feature_tile(d1, &ntf, c->tune.feature_tile) : 0;
         bool ok;
         if (rm) {
           ok = tc_segment_rm(m, 0, Hcb[0], Hcb[1], rows, ldc_b, c->wb_hi + c->wb_a[l],
@@ -438,7 +440,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
       bool ok;
       if (rm) {
         int ntf = 1;
-        const int tf = feature_tile(Ktot, &ntf);
+        const int tf = feature_tile(Ktot, &ntf, c->tune.feature_tile);
         ok = tc_segment_rm(o, 0, Hcb[0], Hcb[1], rows, ldh, c->wb_hi + c->wb_orb,
                            two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb, tf);
         o.rm = 1;
@@ -692,6 +694,7 @@ long chunk_for(fn_ctx* c, long B, int mode) {
   long ch = (long)((budget - base) / per);
   if (ch < 1) ch = 1;
   if (ch > B) ch = B;
+  if (mode == 1 && c->tune.tangent_chunk > 0 && c->tune.tangent_chunk < ch) ch = c->tune.tangent_chunk;
   if (const char* v = getenv("FERMINET_CHUNK")) {
     long f = atol(v);
     if (f > 0 && f < ch) ch = f;
@@ -1230,6 +1233,87 @@ fn_status ferminet_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_st
   CK(cudaGraphLaunch(c->step_exec, gs));
   CK(cudaEventRecord(c->ev_out, gs));
   CK(cudaStreamWaitEvent(user, c->ev_out, 0));
+  return after_launch(c);
+}
+
+fn_status ferminet_get_tuning(const fn_ctx* c, fn_tuning* out) {
+  if (!c || !out) return FN_EINVAL;
+  *out = c->tune;
+  return FN_OK;
+}
+
+fn_status ferminet_set_tuning(fn_ctx* c, const fn_tuning* t) {
+  if (!c || !t) return FN_EINVAL;
+  if (t->layer_groups < 0 || t->feature_tile < 0 || t->tangent_chunk < 0) return fail(c, FN_EINVAL, "negative tuning");
+  if (t->layer_groups > 0 && (t->layer_groups * c->Ct > 256 || (t->layer_groups * c->Ct) % 16))
+    return fail(c, FN_EINVAL, "layer_groups gives an invalid tile");
+  if (t->feature_tile > 0 && (t->feature_tile > 256 || t->feature_tile % 16))
+    return fail(c, FN_EINVAL, "feature_tile must be a multiple of 16 up to 256");
+  c->tune = *t;
+  if (c->step_exec) {  // a captured step holds the old tile shapes
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  return FN_OK;
+}
+
+fn_status ferminet_autotune(fn_ctx* c, const float* d_x, long B, int repeats, fn_tuning* best) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (B < 1) return fail(c, FN_EINVAL, "empty batch");
+  if (repeats < 1) repeats = 1;
+  float* eloc = nullptr;
+  CK(cudaMalloc(&eloc, sizeof(float) * B));
+  std::vector<int> groups = {0};
+  for (int g = 1; g * c->Ct <= 256; ++g)
+    if ((g * c->Ct) % 16 == 0) groups.push_back(g);
+  const std::vector<int> ftiles = {0, 128, 192};
+  const long full = chunk_for(c, B, 1);
+  std::vector<long> chunks = {0};
+  if (full > 1) chunks.push_back((full + 1) / 2);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const fn_tuning saved = c->tune;
+  fn_tuning bestt = saved;
+  float best_ms = 1e30f;
+  for (int g : groups)
+    for (int ft : ftiles)
+      for (long ch : chunks) {
+        c->tune.layer_groups = g;
+        c->tune.feature_tile = ft;
+        c->tune.tangent_chunk = ch;
+        float tmin = 1e30f;
+        for (int r = 0; r <= repeats; ++r) {  // first run warms up (and sizes the workspace)
+          cudaEventRecord(e0, c->stream);
+          st = run_passes(c, d_x, B, true, FwdOut{nullptr, nullptr, eloc, nullptr});
+          cudaEventRecord(e1, c->stream);
+          if (st != FN_OK) break;
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (r > 0 && ms < tmin) tmin = ms;
+        }
+        if (st != FN_OK) break;
+        if (tmin < best_ms) {
+          best_ms = tmin;
+          bestt = c->tune;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(eloc);
+  if (st != FN_OK) {
+    c->tune = saved;
+    return st;
+  }
+  c->tune = bestt;
+  if (c->step_exec) {
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  if (best) *best = bestt;
   return after_launch(c);
 }
 

@@ -215,6 +215,7 @@ struct fn_ctx {
   long wb_total = 0;
   __nv_bfloat16* ident = nullptr;  // 128 x 128 BF16 identity (operand of the folded per-walker term)
   int force64 = 0;
+  fn_tuning tune{};  // 0 fields: defaults
   // captured full step (ferminet_step with use_graph)
   uint64_t* d_counter = nullptr;
   cudaGraphExec_t step_exec = nullptr;

@@ -99,3 +99,22 @@ def test_mixed_chunked_equals_unchunked(monkeypatch):
     monkeypatch.setenv("FERMINET_CHUNK", "5")
     b = fn.local_energy(xx)["eloc"]
     assert torch.equal(a, b)
+
+
+def test_autotune_and_tuning_roundtrip():
+    """The autotuner picks a valid configuration; every tiling gives the same
+    local energies up to the order of floating-point accumulation."""
+    wl, lay, P, x, geo = setup("ne", 64)
+    fn = make(wl, P, "mixed")
+    xx = torch.from_numpy(x).cuda()
+    ref = fn.local_energy(xx)["eloc"].clone()
+    best = fn.autotune(xx, repeats=1)
+    assert fn.get_tuning() == best
+    e = fn.local_energy(xx)["eloc"]
+    assert torch.allclose(e, ref, rtol=1e-6, atol=1e-5)
+    fn.set_tuning(layer_groups=4, feature_tile=128, tangent_chunk=17)
+    e2 = fn.local_energy(xx)["eloc"]
+    assert torch.allclose(e2, ref, rtol=1e-6, atol=1e-5)
+    from paper_2011_07125_gb300.binding import FermiNetError
+    with pytest.raises(FermiNetError):
+        fn.set_tuning(feature_tile=100)
