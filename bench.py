@@ -257,7 +257,7 @@ def run_gpu(args, wl):
     lp = fn.logpsi(x, with_sign=False)
     tuning = None
     if prec == "mixed" and not args.no_autotune:
-        tuning, cached = fn.autotune_cached(x)
+        tuning, cached = fn.autotune_cached(x, repeats=3)
         tuning = dict(tuning, cached=cached)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     counter = [0]

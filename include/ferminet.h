@@ -193,11 +193,17 @@ fn_status ferminet_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_
  *   feature_tile:  features per tile of the rows-on-lanes GEMMs (orbitals and
  *                  per-walker terms; a multiple of 16, <= 256);
  *   tangent_chunk: walkers per local-energy chunk (bounded by the workspace
- *                  budget). */
+ *                  budget);
+ *   residual_smem: 1 = the layer GEMM loads the k-blocks of its residual once
+ *                  into a dedicated shared-memory region used by both the MMAs
+ *                  and the epilogue (less DRAM traffic, shallower pipeline);
+ *                  0 = the epilogue reads the residual from global memory. */
 typedef struct {
   int layer_groups;
   int feature_tile;
   long tangent_chunk;
+  int residual_smem;
+  int pad;
 } fn_tuning;
 
 fn_status ferminet_get_tuning(const fn_ctx* ctx, fn_tuning* out);

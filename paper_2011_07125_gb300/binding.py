@@ -36,7 +36,8 @@ class FnGeometry(C.Structure):
 
 
 class FnTuning(C.Structure):
-    _fields_ = [("layer_groups", C.c_int), ("feature_tile", C.c_int), ("tangent_chunk", C.c_long)]
+    _fields_ = [("layer_groups", C.c_int), ("feature_tile", C.c_int), ("tangent_chunk", C.c_long),
+                ("residual_smem", C.c_int), ("pad", C.c_int)]
 
 
 class FnParamEntry(C.Structure):
@@ -278,13 +279,18 @@ class FermiNet:
                                                    C.byref(fl)), "ferminet_profile_read")
         return {"ms": ms.value, "launches": n.value, "alg_flops": fl.value}
 
+    @staticmethod
+    def _tdict(t):
+        return {"layer_groups": t.layer_groups, "feature_tile": t.feature_tile, "tangent_chunk": t.tangent_chunk,
+                "residual_smem": t.residual_smem}
+
     def get_tuning(self):
         t = FnTuning()
         self._check(self.lib.ferminet_get_tuning(self.ctx, C.byref(t)), "ferminet_get_tuning")
-        return {"layer_groups": t.layer_groups, "feature_tile": t.feature_tile, "tangent_chunk": t.tangent_chunk}
+        return self._tdict(t)
 
-    def set_tuning(self, layer_groups=0, feature_tile=0, tangent_chunk=0):
-        t = FnTuning(int(layer_groups), int(feature_tile), int(tangent_chunk))
+    def set_tuning(self, layer_groups=0, feature_tile=0, tangent_chunk=0, residual_smem=0):
+        t = FnTuning(int(layer_groups), int(feature_tile), int(tangent_chunk), int(residual_smem), 0)
         self._check(self.lib.ferminet_set_tuning(self.ctx, C.byref(t)), "ferminet_set_tuning")
 
     def autotune(self, x, repeats=2):
@@ -293,7 +299,7 @@ class FermiNet:
         self._f32(x, (B, self.n, 3))
         t = FnTuning()
         self._check(self.lib.ferminet_autotune(self.ctx, _ptr(x), B, int(repeats), C.byref(t)), "ferminet_autotune")
-        return {"layer_groups": t.layer_groups, "feature_tile": t.feature_tile, "tangent_chunk": t.tangent_chunk}
+        return self._tdict(t)
 
     def autotune_cached(self, x, cache_path=None, repeats=2):
         """Tuning from a JSON cache keyed by network shape, batch, precision and

@@ -416,6 +416,8 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         m.ldu = d1;
         m.res_hi = l >= 1 ? Hcb[0] : nullptr;
         m.res_lo = (l >= 1 && two) ? Hcb[1] : nullptr;
+        // the residual h^l is segment 0's B operand: read it from shared memory
+        m.res_smem = (tangent && l >= 1 && !rm && c->tune.residual_smem == 1) ? 1 : 0;
         m.hb_hi = Hnb[0];
         m.hb_lo = two ? Hnb[1] : nullptr;
         m.ldhb = ldh;
@@ -1244,7 +1246,9 @@ fn_status ferminet_get_tuning(const fn_ctx* c, fn_tuning* out) {
 
 fn_status ferminet_set_tuning(fn_ctx* c, const fn_tuning* t) {
   if (!c || !t) return FN_EINVAL;
-  if (t->layer_groups < 0 || t->feature_tile < 0 || t->tangent_chunk < 0) return fail(c, FN_EINVAL, "negative tuning");
+  if (t->layer_groups < 0 || t->feature_tile < 0 || t->tangent_chunk < 0 || t->residual_smem < 0 ||
+      t->residual_smem > 1)
+    return fail(c, FN_EINVAL, "bad tuning value");
   if (t->layer_groups > 0 && (t->layer_groups * c->Ct > 256 || (t->layer_groups * c->Ct) % 16))
     return fail(c, FN_EINVAL, "layer_groups gives an invalid tile");
   if (t->feature_tile > 0 && (t->feature_tile > 256 || t->feature_tile % 16))
@@ -1280,10 +1284,12 @@ fn_status ferminet_autotune(fn_ctx* c, const float* d_x, long B, int repeats, fn
   float best_ms = 1e30f;
   for (int g : groups)
     for (int ft : ftiles)
-      for (long ch : chunks) {
+      for (long ch : chunks)
+        for (int rs = 0; rs < 2; ++rs) {
         c->tune.layer_groups = g;
         c->tune.feature_tile = ft;
         c->tune.tangent_chunk = ch;
+        c->tune.residual_smem = rs;
         float tmin = 1e30f;
         for (int r = 0; r <= repeats; ++r) {  // first run warms up (and sizes the workspace)
           cudaEventRecord(e0, c->stream);
@@ -1300,7 +1306,7 @@ fn_status ferminet_autotune(fn_ctx* c, const float* d_x, long B, int repeats, fn
           best_ms = tmin;
           bestt = c->tune;
         }
-      }
+        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(eloc);

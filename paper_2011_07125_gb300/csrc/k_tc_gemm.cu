@@ -36,11 +36,12 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;            // 64 bf16 = 128 bytes: one swizzle row
-constexpr int STAGES = 4;
+constexpr int STAGES = 4;  // at most; fewer when the residual region needs the space
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES_MAX = 256 * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES_MAX;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int SMEM_BYTES = 227 * 1024;  // dynamic shared memory requested per CTA
+constexpr int BAR_BYTES = 256;
 constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
@@ -145,14 +146,66 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Work items of one tile, in issue order: every (segment, k-block, term)
+// except, when the epilogue takes its residual from shared memory (mode 1 with
+// a residual), segment 0's k-blocks that hold this m-tile's 128 features; those
+// come last and their B tiles (hi and lo) go to a dedicated shared-memory
+// region that both the MMAs and the epilogue read.
+struct Item {
+  int sg, kb, t;
+  bool res;
+};
+
+__device__ __forceinline__ int res_blocks(const TcGemmArgs& a, int tm) {
+  if (!a.res_smem) return 0;
+  const int nr = a.kblocks[0] - 2 * tm;
+  return nr < 0 ? 0 : (nr > 2 ? 2 : nr);
+}
+
+__device__ __forceinline__ int tile_items(const TcGemmArgs& a, int tm) {
+  int n = 0;
+  for (int sg = 0; sg < a.nseg; ++sg) n += a.kblocks[sg] * a.seg_terms[sg];
+  return n;
+}
+
+__device__ __forceinline__ Item item_at(const TcGemmArgs& a, int tm, int nres, int i) {
+  Item it;
+  it.res = false;
+  for (int sg = 0; sg < a.nseg; ++sg) {
+    const int nt = a.seg_terms[sg];
+    const int cnt = a.kblocks[sg] * nt - (sg == 0 ? nres * nt : 0);
+    if (i < cnt) {
+      it.sg = sg;
+      it.t = i % nt;
+      int kb = i / nt;
+      if (sg == 0 && nres > 0 && kb >= 2 * tm) kb += nres;
+      it.kb = kb;
+      return it;
+    }
+    i -= cnt;
+  }
+  const int nt0 = a.seg_terms[0];
+  it.sg = 0;
+  it.kb = 2 * tm + i / nt0;
+  it.t = i % nt0;
+  it.res = true;
+  return it;
+}
+
 __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ TcGemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  const int nst = a.stages;
+  const int stage_bytes = A_BYTES + a.tile_n * BK * 2;
+  uint8_t* resr = smem + nst * stage_bytes;                   // residual region (1024-aligned)
+  const int res_half = 2 * a.tile_n * BK * 2;                 // two k-blocks of one part (hi or lo)
+  uint64_t* full = reinterpret_cast<uint64_t*>(resr + (a.res_smem ? 2 * res_half : 0));
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* rfull = tempty + 2;
+  uint64_t* rempty = rfull + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -165,6 +218,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       mbar_init(&tfull[s], 1);
       mbar_init(&tempty[s], EPI_WARPS);
     }
+    mbar_init(rfull, 1);
+    mbar_init(rempty, EPI_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -193,81 +248,114 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
   if (warp == 0) {
     if (lane == 0) {
       int stage = 0;
-      uint32_t phase = 0;
+      uint32_t phase = 0, rphase = 0;
       for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int tn = (int)(tile / a.n_tiles_m), tm = (int)(tile % a.n_tiles_m);
+        const int nres = res_blocks(a, tm);
+        const int nit = tile_items(a, tm);
         bool ok = true;
-        for (int sg = 0; sg < a.nseg && ok; ++sg)
-          for (int kb = 0; kb < a.kblocks[sg] && ok; ++kb)
-            for (int t = 0; t < a.seg_terms[sg] && ok; ++t) {
-              if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status)) {
-                ok = false;
-                break;
-              }
-              const int ai = (t == 2) ? 1 : 0, bi = (t == 1) ? 1 : 0;
-              uint8_t* sa = smem + stage * STAGE_BYTES;
-              uint8_t* sb = sa + A_BYTES;
-              mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
-              if (a.seg_group[sg] == 0) {
-                tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
-                tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
-              } else {
-                // identity weights for this m-tile's 64-feature block; B rows
-                // gathered per group from the per-walker tensor
-                const int G = a.seg_group[sg];
-                tma_load_2d(sa, &a.A[sg][ai], kb * BK, 0, &full[stage]);
-                for (int g0 = 0; g0 < tile_n; g0 += G) {
-                  long r0 = (long)tn * tile_n + g0;
-                  if (r0 >= a.rows) r0 = a.rows - G;  // past the end: any in-range rows (unused)
-                  const int y = (int)((r0 / a.u_div) * G);
-                  tma_load_2d(sb + (size_t)g0 * BK * 2, &a.B[sg][bi], tm * BM + kb * BK, y, &full[stage]);
-                }
-              }
-              if (++stage == STAGES) {
-                stage = 0;
-                phase ^= 1;
-              }
+        for (int i = 0; i < nit && ok; ++i) {
+          const Item it = item_at(a, tm, nres, i);
+          if (it.res && it.kb == 2 * tm && it.t == 0) {
+            // the residual region is free once the previous tile's epilogue is done
+            if (!mbar_wait(rempty, rphase ^ 1, abort_flag, a.status)) {
+              ok = false;
+              break;
             }
+            const int nparts = a.seg_terms[0] > 1 ? 2 : 1;
+            mbar_expect_tx(rfull, (uint32_t)(nparts * nres * a.tile_n * BK * 2));
+            for (int h = 0; h < nparts; ++h)
+              for (int r = 0; r < nres; ++r)
+                tma_load_2d(resr + h * res_half + r * (a.tile_n * BK * 2), &a.B[0][h], (2 * tm + r) * BK,
+                            tn * tile_n, rfull);
+          }
+          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          const int ai = (it.t == 2) ? 1 : 0, bi = (it.t == 1) ? 1 : 0;
+          uint8_t* sa = smem + stage * stage_bytes;
+          uint8_t* sb = sa + A_BYTES;
+          const int sg = it.sg, kb = it.kb;
+          if (it.res) {
+            mbar_expect_tx(&full[stage], A_BYTES);
+            tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
+          } else if (a.seg_group[sg] == 0) {
+            mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
+            tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
+            tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
+          } else {
+            // identity weights for this m-tile's 64-feature block; B rows
+            // gathered per group from the per-walker tensor
+            mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
+            const int G = a.seg_group[sg];
+            tma_load_2d(sa, &a.A[sg][ai], kb * BK, 0, &full[stage]);
+            for (int g0 = 0; g0 < tile_n; g0 += G) {
+              long r0 = (long)tn * tile_n + g0;
+              if (r0 >= a.rows) r0 = a.rows - G;  // past the end: any in-range rows (unused)
+              const int y = (int)((r0 / a.u_div) * G);
+              tma_load_2d(sb + (size_t)g0 * BK * 2, &a.B[sg][bi], tm * BM + kb * BK, y, &full[stage]);
+            }
+          }
+          if (++stage == nst) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
         if (!ok) break;
+        if (nres > 0) rphase ^= 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = make_idesc(BM, tile_n);
       int stage = 0;
-      uint32_t phase = 0;
+      uint32_t phase = 0, rphase = 0;
       int acc = 0;
       uint32_t acc_phase = 0;
       for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const int tm = (int)(tile % a.n_tiles_m);
+        const int nres = res_blocks(a, tm);
+        const int nit = tile_items(a, tm);
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, a.status)) break;
         fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
         bool ok = true;
         uint32_t first = 1;
-        for (int sg = 0; sg < a.nseg && ok; ++sg)
-          for (int kb = 0; kb < a.kblocks[sg] && ok; ++kb)
-            for (int t = 0; t < a.seg_terms[sg] && ok; ++t) {
-              if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
-                ok = false;
-                break;
-              }
-              fence_after();
-              const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
-              const uint32_t sb = sa + A_BYTES;
-              const uint64_t da = smem_desc(sa), db = smem_desc(sb);
-#pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                // 16 bf16 = 32 bytes along K inside the swizzle row: +2 in the address field
-                mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, first ? 0u : 1u);
-                first = 0;
-              }
-              mma_commit(&empty[stage]);
-              if (++stage == STAGES) {
-                stage = 0;
-                phase ^= 1;
-              }
+        for (int i = 0; i < nit && ok; ++i) {
+          const Item it = item_at(a, tm, nres, i);
+          if (it.res && it.kb == 2 * tm && it.t == 0) {
+            if (!mbar_wait(rfull, rphase, abort_flag, a.status)) {
+              ok = false;
+              break;
             }
+          }
+          if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = smem_u32(smem + stage * stage_bytes);
+          uint32_t sb = sa + A_BYTES;
+          if (it.res) {
+            const int bi = (it.t == 1) ? 1 : 0;
+            sb = smem_u32(resr + bi * res_half + (it.kb - 2 * tm) * (a.tile_n * BK * 2));
+          }
+          const uint64_t da = smem_desc(sa), db = smem_desc(sb);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            // 16 bf16 = 32 bytes along K inside the swizzle row: +2 in the address field
+            mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, first ? 0u : 1u);
+            first = 0;
+          }
+          mma_commit(&empty[stage]);
+          if (++stage == nst) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
         if (!ok) break;
+        if (nres > 0) rphase ^= 1;
         mma_commit(&tfull[acc]);
         if (++acc == 2) {
           acc = 0;
@@ -289,11 +377,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     __nv_bfloat16* __restrict__ ol = a.hb_lo;
     float* __restrict__ out = a.out;
     int acc = 0;
-    uint32_t acc_phase = 0;
+    uint32_t acc_phase = 0, rphase = 0;
     for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       const int tn = (int)(tile / a.n_tiles_m), tm = (int)(tile % a.n_tiles_m);
+      const int nres = res_blocks(a, tm);
       if (!mbar_wait(&tfull[acc], acc_phase, abort_flag, a.status)) break;
       fence_after();
+      // residual tiles in shared memory: acquire the TMA writes
+      if (nres > 0 && !mbar_wait(rfull, rphase, abort_flag, a.status)) break;
       const int f = tm * BM + lane_base + lane;
       const bool fok = f < a.mfeat;
       const uint32_t tbase = tmem_base + ((uint32_t)lane_base << 16) + (uint32_t)(acc * 256);
@@ -474,8 +565,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
           const float y = tanhf(z0);
           const float s = 1.f - y * y;
           const float lapc = -2.f * y * s * sq;
-          const __nv_bfloat16* __restrict__ rhg = rh ? rh + rb : nullptr;
-          const __nv_bfloat16* __restrict__ rlg = rl ? rl + rb : nullptr;
+          const __nv_bfloat16* __restrict__ rhg = (rh && !a.res_smem) ? rh + rb : nullptr;
+          const __nv_bfloat16* __restrict__ rlg = (rl && !a.res_smem) ? rl + rb : nullptr;
+          // residual in the shared region: 128-byte swizzled rows of 64 features
+          const int fl = lane_base + lane;
+          const int kbl = fl >> 6, fk = fl & 63;
+          const bool sres = nres > 0 && kbl < nres;
+          const uint8_t* rsh = resr + kbl * (a.tile_n * BK * 2) + ((fk & 7) << 1);
+          const int chunk = fk >> 3;
+          const bool slo = a.res_lo != nullptr;
           __nv_bfloat16* __restrict__ ohg = oh + rb;
           __nv_bfloat16* __restrict__ olg = ol ? ol + rb : nullptr;
           // pass 2: outputs (+ residual), stored as BF16 hi + lo; the global
@@ -488,6 +586,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
               float v = 0.f;
               if (gok && rhg) v += __bfloat162float(rhg[off]);
               if (gok && rlg) v += __bfloat162float(rlg[off]);
+              if (gok && sres) {
+                const int rl_ = gi * C + c0 + j;  // row within the tile
+                const int so = rl_ * 128 + ((chunk ^ (rl_ & 7)) << 4);
+                v += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(rsh + so));
+                if (slo) v += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(rsh + res_half + so));
+              }
               r8[j] = v;
             }
           };
@@ -522,7 +626,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (lane == 0) {
+        mbar_arrive(&tempty[acc]);
+        if (nres > 0) mbar_arrive(rempty);
+      }
+      if (nres > 0) rphase ^= 1;
       if (++acc == 2) {
         acc = 0;
         acc_phase ^= 1;
@@ -580,11 +688,20 @@ int tc_num_sms() {
   return n;
 }
 
-fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a) {
+fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
+  TcGemmArgs a = a0;
+  // ring depth from the shared memory left after the residual region
+  const int stage_bytes = A_BYTES + a.tile_n * BK * 2;
+  const int res_bytes = a.res_smem ? 4 * a.tile_n * BK * 2 : 0;
+  const int avail = SMEM_BYTES - 1024 - BAR_BYTES - res_bytes;
+  a.stages = avail / stage_bytes;
+  if (a.stages > STAGES) a.stages = STAGES;
+  if (a.stages < 2) return FN_EINVAL;
+  if (a.res_smem && (a.mode != 1 || a.tile_n % 8)) return FN_EINVAL;
   if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.nseg < 1 || a.nseg > 3 || a.mode < 0 || a.mode > 2)
     return FN_EINVAL;
   if (a.rm && (a.mode == 1 || (a.mode == 2 && (a.mfeat % 8 || a.ldu % 4 || a.ldhb % 8)) ||

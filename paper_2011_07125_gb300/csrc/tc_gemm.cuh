@@ -18,6 +18,10 @@ struct TcGemmArgs {
   int seg_group[3];       // 0: B rows contiguous; C: B tile gathered per group of C
                           // rows from row (r0 / u_div) * C of the segment's tensor
   int nseg, terms;        // terms 1: hi*hi; 3: hi*hi + hi*lo + lo*hi
+  int stages;             // shared-memory ring depth (set by tc_gemm_launch)
+  int res_smem;           // mode 1: the residual is segment 0's B operand; its two
+                          // k-blocks holding the tile's features are loaded once into a
+                          // dedicated region read by both the MMAs and the epilogue
   long rows;              // activation rows (N dimension)
   int mfeat;              // output features (M dimension)
   int tile_n;             // rows per tile: multiple of 16, <= 256
