@@ -159,6 +159,26 @@ fn_status ferminet_logpsi_vjp(fn_ctx* ctx, const float* d_x, long B, const float
 fn_status ferminet_energy_grad(fn_ctx* ctx, const float* d_x, long B, const float* d_eloc, double* d_emean,
                                float* d_grad);
 
+/* Replica form of ferminet_energy_grad, for a batch whose walkers are split over
+ * several processes (data parallelism over walkers; Eq. 2's expectation is a
+ * mean over every walker of the batch).  The gradient weights each walker by
+ * E_L,w minus the mean over the whole batch, so it takes two exchanges:
+ *   1. ferminet_energy_sums: d_sums [n_geoms] (double) = FP64 sum of d_eloc
+ *      over this process's walkers of each geometry.  The caller adds d_sums
+ *      and the walker counts over the processes and divides (E_mean,g).
+ *   2. ferminet_energy_grad_partial: d_grad64 [n_params] (double) =
+ *      sum_g 2/count_g sum_{w of g here} (E_L,w - d_emean[g]) d log|psi_w|/d theta,
+ *      with d_emean and d_count [n_geoms] (double) over the whole batch,
+ *      accumulated in FP64.  The sum of d_grad64 over the processes is the
+ *      gradient ferminet_energy_grad computes on the whole batch.
+ * With one process (count_g = this batch's) the two calls reproduce
+ * ferminet_energy_grad.  A geometry with walkers here must have count_g > 0.
+ * B follows the rules of ferminet_energy_grad (with several geometries, B
+ * equals the walker total of the geometry table). */
+fn_status ferminet_energy_sums(fn_ctx* ctx, const float* d_eloc, long B, double* d_sums);
+fn_status ferminet_energy_grad_partial(fn_ctx* ctx, const float* d_x, long B, const float* d_eloc,
+                                       const double* d_emean, const double* d_count, double* d_grad64);
+
 /* n_steps Gaussian all-electron Metropolis moves sampling |psi|^2 (Eq. 2).
  * Step s uses counter t = counter + s.  For walker w the proposal is
  * x' = x + width * z with z drawn by Philox4x32-10 (key {seed lo, seed hi},

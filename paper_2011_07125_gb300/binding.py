@@ -60,7 +60,7 @@ class FermiNetError(RuntimeError):
 
 EXPORTS = ("ferminet_init", "ferminet_param_layout", "ferminet_net_layout", "ferminet_set_params",
            "ferminet_logpsi", "ferminet_local_energy", "ferminet_logpsi_vjp", "ferminet_energy_grad",
-           "ferminet_mcmc_step", "ferminet_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
+           "ferminet_energy_sums", "ferminet_energy_grad_partial", "ferminet_mcmc_step", "ferminet_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
            "ferminet_profile_read", "ferminet_launch_count", "ferminet_get_tuning", "ferminet_set_tuning",
            "ferminet_autotune", "ferminet_last_error", "ferminet_destroy")
 KERNEL_CLASSES = {"tangent_gemm": 0, "det_tangent": 1, "two_layer": 2, "means": 3, "tanh": 4, "value_pass": 5,
@@ -91,6 +91,8 @@ def load(path: Optional[str] = None):
         lib.ferminet_local_energy.argtypes = [vp, vp, C.c_long, vp, vp, vp, vp]
         lib.ferminet_logpsi_vjp.argtypes = [vp, vp, C.c_long, vp, vp]
         lib.ferminet_energy_grad.argtypes = [vp, vp, C.c_long, vp, vp, vp]
+        lib.ferminet_energy_sums.argtypes = [vp, vp, C.c_long, vp]
+        lib.ferminet_energy_grad_partial.argtypes = [vp, vp, C.c_long, vp, vp, vp, vp]
         lib.ferminet_mcmc_step.argtypes = [vp, vp, vp, C.c_long, C.c_int, C.c_float, C.c_uint64, C.c_uint64, vp]
         lib.ferminet_step.argtypes = [vp, vp, vp, C.c_long, C.c_int, C.c_float, C.c_uint64, C.c_uint64, vp, vp, vp,
                                       vp, C.c_int]
@@ -164,6 +166,7 @@ class FermiNet:
             garr[i].walker_count = int(counts[i])
             off += int(counts[i])
         self.total = off
+        self.counts = [int(c) for c in counts]
         self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = C.c_void_p()
@@ -238,6 +241,33 @@ class FermiNet:
         self._check(self.lib.ferminet_energy_grad(self.ctx, _ptr(x), B, _ptr(eloc), _ptr(em), _ptr(g)),
                     "ferminet_energy_grad")
         return em, g
+
+    def walker_counts(self, B):
+        """Walkers of each geometry in a batch of B (float64 [G], on the GPU)."""
+        c = [B] if self.G == 1 else self.counts
+        return self.torch.tensor(c, dtype=self.torch.float64, device="cuda")
+
+    def energy_sums(self, eloc):
+        """FP64 sum of eloc over each geometry's walkers (float64 [G])."""
+        B = eloc.shape[0]
+        self._f32(eloc, (B,))
+        s = self._empty(self.G, dtype=self.torch.float64)
+        self._check(self.lib.ferminet_energy_sums(self.ctx, _ptr(eloc), B, _ptr(s)), "ferminet_energy_sums")
+        return s
+
+    def energy_grad_partial(self, x, eloc, emean, count):
+        """This process's share of the VMC gradient given the mean energy and
+        walker count of every geometry over the whole batch (float64 [P])."""
+        B = x.shape[0]
+        self._f32(x, (B, self.n, 3))
+        self._f32(eloc, (B,))
+        for t in (emean, count):
+            if not (t.is_cuda and t.dtype == self.torch.float64 and t.is_contiguous() and t.numel() == self.G):
+                raise FermiNetError(f"expected a contiguous float64 CUDA tensor of {self.G} elements")
+        g = self._empty(self.n_params, dtype=self.torch.float64)
+        self._check(self.lib.ferminet_energy_grad_partial(self.ctx, _ptr(x), B, _ptr(eloc), _ptr(emean), _ptr(count),
+                                                          _ptr(g)), "ferminet_energy_grad_partial")
+        return g
 
     def mcmc_step(self, x, logpsi, n_steps, width, seed, counter, accepted=None):
         """Advances x and logpsi in place; returns the accepted-move counts."""

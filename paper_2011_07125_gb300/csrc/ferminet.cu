@@ -776,9 +776,13 @@ fn_status run_passes(fn_ctx* c, const float* x, long B, bool tangent, const FwdO
   return after_launch(c);
 }
 
-fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* grad) {
+// Accumulates sum_w seeds[w] d log|psi_w| / d theta in FP64 into grad64 (the
+// context's buffer unless the caller supplies one); stores it as float into
+// grad when grad is given.
+fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* grad, double* grad64 = nullptr) {
   cudaStream_t s = c->stream;
-  launch_zero_d(s, c->d_grad64, c->lay.total);
+  if (!grad64) grad64 = c->d_grad64;
+  launch_zero_d(s, grad64, c->lay.total);
   if (B > 0) {
     const long ch = chunk_for(c, B, 2);
     fn_status st = ensure_ws(c, ws_bytes(c, ch, 2));
@@ -790,10 +794,10 @@ fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* 
       ar.measure = false;
       ar.base = c->ws;
       Prof pa(c, FN_KC_ADJOINT, 0.0);
-      vjp_chunk(c, ar, x + w0 * n3, Bc, w0, seeds + w0, c->d_grad64);
+      vjp_chunk(c, ar, x + w0 * n3, Bc, w0, seeds + w0, grad64);
     }
   }
-  launch_d2f(s, c->d_grad64, grad, c->lay.total);
+  if (grad) launch_d2f(s, grad64, grad, c->lay.total);
   return after_launch(c);
 }
 
@@ -896,7 +900,7 @@ fn_status run_step(fn_ctx* c, float* x, float* lp, long B, int n_steps, float wi
   }
   fn_status st = run_passes(c, x, B, true, FwdOut{nullptr, nullptr, eloc, nullptr});
   if (st != FN_OK) return st;
-  const long B1 = c->G > 1 ? 0 : B;
+  const long B1 = c->G > 1 ? -1 : B;
   launch_emean(c->stream, eloc, c->G, c->d_geo_off, c->d_geo_cnt, B1, emean);
   launch_seeds(c->stream, eloc, B, c->G > 1 ? c->d_geo : nullptr, emean, c->d_geo_cnt, B1, seeds);
   return run_vjp(c, x, B, seeds, grad);
@@ -1130,10 +1134,34 @@ fn_status ferminet_energy_grad(fn_ctx* c, const float* d_x, long B, const float*
   st = ensure_aux(c, std::max<long>(B, 1));
   if (st != FN_OK) return st;
   float* seeds = c->aux;
-  const long B1 = c->G > 1 ? 0 : B;
+  const long B1 = c->G > 1 ? -1 : B;
   launch_emean(c->stream, d_eloc, c->G, c->d_geo_off, c->d_geo_cnt, B1, d_emean);
   launch_seeds(c->stream, d_eloc, B, c->G > 1 ? c->d_geo : nullptr, d_emean, c->d_geo_cnt, B1, seeds);
   return run_vjp(c, d_x, B, seeds, d_grad);
+}
+
+fn_status ferminet_energy_sums(fn_ctx* c, const float* d_eloc, long B, double* d_sums) {
+  if (!c) return FN_EINVAL;
+  if (B < 0) return fail(c, FN_EINVAL, "negative batch size");
+  if (c->G > 1 && B != c->geo_total)
+    return fail(c, FN_EINVAL, "batch size must equal the walker total of the geometry table");
+  if (!d_sums || (!d_eloc && B > 0)) return fail(c, FN_EINVAL, "null eloc or sums pointer");
+  launch_esum(c->stream, d_eloc, c->G, c->d_geo_off, c->d_geo_cnt, c->G > 1 ? -1 : B, d_sums);
+  return after_launch(c);
+}
+
+fn_status ferminet_energy_grad_partial(fn_ctx* c, const float* d_x, long B, const float* d_eloc,
+                                       const double* d_emean, const double* d_count, double* d_grad64) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (!d_grad64 || !d_emean || !d_count || (!d_eloc && B > 0))
+    return fail(c, FN_EINVAL, "null eloc, emean, count or grad pointer");
+  st = ensure_aux(c, std::max<long>(B, 1));
+  if (st != FN_OK) return st;
+  float* seeds = c->aux;
+  launch_seeds_given(c->stream, d_eloc, B, c->G > 1 ? c->d_geo : nullptr, d_emean, d_count, seeds);
+  return run_vjp(c, d_x, B, seeds, nullptr, d_grad64);
 }
 
 fn_status ferminet_mcmc_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_steps, float width, uint64_t seed,

@@ -134,12 +134,18 @@ void launch_propose(cudaStream_t s, const float* x, float* xp, long B, int n3, f
 void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, const float* lp_prop, long B, int n3,
                    uint64_t seed, uint64_t t, int* accepted, const uint64_t* dctr);
 void launch_set_u64(cudaStream_t s, uint64_t* p, uint64_t v);
-// With G == 1 the single geometry holds all B walkers (B1 = B); otherwise the
-// device tables d_off / d_cnt give each geometry's walker range.
+// With G == 1 the single geometry holds all B walkers (B1 = B >= 0); with
+// B1 < 0 the device tables d_off / d_cnt give each geometry's walker range.
+// launch_esum writes sums instead of means; launch_seeds_given takes the mean
+// and the walker count of every geometry over the whole (replicated) batch.
 void launch_emean(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
                   double* emean);
 void launch_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
                   const long* d_cnt, long B1, float* seeds);
+void launch_esum(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
+                 double* sums);
+void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
+                        const double* count, float* seeds);
 void launch_d2f(cudaStream_t s, const double* a, float* b, long n);
 void launch_fill(cudaStream_t s, float* p, float v, long n);
 void launch_zero_d(cudaStream_t s, double* p, long n);

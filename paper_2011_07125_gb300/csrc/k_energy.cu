@@ -179,12 +179,13 @@ __global__ void k_accept(float* __restrict__ x, const float* __restrict__ xp, fl
   }
 }
 
-// One block per geometry: deterministic tree sum in FP64.
+// One block per geometry: deterministic tree sum in FP64; the mean when
+// `mean` is set, else the sum.
 __global__ void k_emean(const float* __restrict__ eloc, const long* __restrict__ off, const long* __restrict__ cnt,
-                        long B1, double* emean) {
+                        long B1, int mean, double* emean) {
   __shared__ double sh[256];
   const int g = blockIdx.x;
-  const long o = B1 > 0 ? 0 : off[g], c = B1 > 0 ? B1 : cnt[g];
+  const long o = B1 >= 0 ? 0 : off[g], c = B1 >= 0 ? B1 : cnt[g];
   double s = 0.0;
   for (long i = threadIdx.x; i < c; i += 256) s += (double)eloc[o + i];
   sh[threadIdx.x] = s;
@@ -193,7 +194,7 @@ __global__ void k_emean(const float* __restrict__ eloc, const long* __restrict__
     if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) emean[g] = c > 0 ? sh[0] / (double)c : 0.0;
+  if (threadIdx.x == 0) emean[g] = !mean ? sh[0] : (c > 0 ? sh[0] / (double)c : 0.0);
 }
 
 __global__ void k_seeds(const float* __restrict__ eloc, long B, const int* __restrict__ geo,
@@ -201,8 +202,18 @@ __global__ void k_seeds(const float* __restrict__ eloc, long B, const int* __res
   long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= B) return;
   int g = geo ? geo[w] : 0;
-  double c = B1 > 0 ? (double)B1 : (double)cnt[g];
+  double c = B1 >= 0 ? (double)B1 : (double)cnt[g];
   seeds[w] = (float)(2.0 * ((double)eloc[w] - emean[g]) / c);
+}
+
+// Seeds of the replica form: the mean and the count are those of the whole
+// batch over all replicas.
+__global__ void k_seeds_given(const float* __restrict__ eloc, long B, const int* __restrict__ geo,
+                              const double* __restrict__ emean, const double* __restrict__ count, float* seeds) {
+  long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= B) return;
+  int g = geo ? geo[w] : 0;
+  seeds[w] = (float)(2.0 * ((double)eloc[w] - emean[g]) / count[g]);
 }
 
 __global__ void k_d2f(const double* a, float* b, long n) {
@@ -248,7 +259,17 @@ void launch_set_u64(cudaStream_t s, uint64_t* p, uint64_t v) { FN_COUNT(1), k_se
 
 void launch_emean(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
                   double* emean) {
-  if (G > 0) FN_COUNT(1), k_emean<<<G, 256, 0, s>>>(eloc, d_off, d_cnt, B1, emean);
+  if (G > 0) FN_COUNT(1), k_emean<<<G, 256, 0, s>>>(eloc, d_off, d_cnt, B1, 1, emean);
+}
+
+void launch_esum(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
+                 double* sums) {
+  if (G > 0) FN_COUNT(1), k_emean<<<G, 256, 0, s>>>(eloc, d_off, d_cnt, B1, 0, sums);
+}
+
+void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
+                        const double* count, float* seeds) {
+  if (B > 0) FN_COUNT(1), k_seeds_given<<<nblk(B, 256), 256, 0, s>>>(eloc, B, geo, emean, count, seeds);
 }
 
 void launch_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean, const long* d_cnt,

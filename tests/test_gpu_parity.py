@@ -190,7 +190,67 @@ def test_empty_batch_and_bad_batch():
     fn1 = make(wl1, P1)
     lp, sg = fn1.logpsi(cuda(x1[:0]))
     assert lp.numel() == 0
+    # an empty batch of a one-geometry context whose table lists walkers
+    e0 = torch.zeros(0, device="cuda")
+    em, g = fn1.energy_grad(cuda(x1[:0]), e0)
+    assert float(em[0]) == 0.0 and float(g.abs().max()) == 0.0
+    assert float(fn1.energy_sums(e0)[0]) == 0.0
     assert fn1.sync() == "FN_OK"
+
+
+@pytest.mark.parametrize("name,per", [("li", 32), ("c4h4x8", 2)])
+def test_replica_calls_reproduce_energy_grad(name, per):
+    """One replica: energy sums + gradient share with the batch's own mean and
+    count give ferminet_energy_grad's result (same seeds, same FP64 sums)."""
+    from paper_2011_07125_gb300 import replicas
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P)
+    eloc = (np.random.default_rng(4).standard_normal(x.shape[0]) * 2 - 7).astype(np.float32)
+    xx, ee = cuda(x), cuda(eloc)
+    sums = fn.energy_sums(ee).cpu().numpy()
+    ref = np.array([eloc[geo == g].astype(np.float64).sum() for g in range(len(wl.geoms))])
+    np.testing.assert_allclose(sums, ref, rtol=1e-13, atol=1e-12)
+    em, g = fn.energy_grad(xx, ee)
+    em_r, g_r = replicas.energy_grad(fn, xx, ee)
+    np.testing.assert_allclose(em_r.cpu().numpy(), em.cpu().numpy(), rtol=1e-15, atol=0)
+    np.testing.assert_allclose(g_r.float().cpu().numpy(), g.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    assert fn.sync() == "FN_OK"
+
+
+@pytest.mark.parametrize("name,per", [("li", 32), ("c4h4x8", 3)])
+def test_two_replicas_add_to_whole_batch(name, per):
+    """Two replicas, each with its own context and half of every geometry's
+    walkers, run one after the other on this GPU; their shares, added on the
+    host as the all-reduces would, equal the oracle's whole-batch gradient."""
+    wl, lay, P, x, geo = setup(name, per)
+    eloc = (np.random.default_rng(4).standard_normal(x.shape[0]) * 2 - 7).astype(np.float32)
+    G = len(wl.geoms)
+    halves = []
+    for r in range(2):
+        idx, cnt, off = [], [], 0
+        for c in wl.counts:
+            lo, hi = off + (0 if r == 0 else c // 2), off + (c // 2 if r == 0 else c)
+            idx.extend(range(lo, hi))
+            cnt.append(hi - lo)
+            off += c
+        halves.append((np.array(idx), cnt))
+    fns = []
+    for idx, cnt in halves:
+        from paper_2011_07125_gb300.binding import FermiNet
+        f = FermiNet(wl.net, wl.geoms, counts=cnt, precision="fp32")
+        f.set_params(cuda(P))
+        fns.append((f, cuda(x[idx]), cuda(eloc[idx])))
+    sums = sum(f.energy_sums(e) for f, _, e in fns)
+    cnts = sum(f.walker_counts(xr.shape[0]) for f, xr, _ in fns)
+    emean = sums / cnts
+    grad = sum(f.energy_grad_partial(xr, e, emean, cnts) for f, xr, e in fns)
+    em_o, g_o = oracle.energy_grad(wl.net, P, wl.geoms, x, eloc, geo=geo)
+    np.testing.assert_allclose(emean.cpu().numpy(), em_o, rtol=1e-12, atol=1e-12)
+    err = np.linalg.norm(grad.cpu().numpy() - g_o) / np.linalg.norm(g_o)
+    print(name, "two-replica energy grad rel L2", err)
+    assert err < TOL_GRAD_FP32
+    for f, _, _ in fns:
+        assert f.sync() == "FN_OK"
 
 
 def test_singular_walker_reported():
