@@ -217,13 +217,18 @@ fn_status ferminet_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_
  *   residual_smem: 1 = the layer GEMM loads the k-blocks of its residual once
  *                  into a dedicated shared-memory region used by both the MMAs
  *                  and the epilogue (less DRAM traffic, shallower pipeline);
- *                  0 = the epilogue reads the residual from global memory. */
+ *                  0 = the epilogue reads the residual from global memory;
+ *   pair_unfused:  1 = the two-electron layer and the spin means of the
+ *                  two-electron stream run as separate kernels (the plain
+ *                  schedule, kept for comparison and for shapes the fused
+ *                  kernel does not cover); 0 = one fused pass (default).
+ *                  Not varied by the autotuner. */
 typedef struct {
   int layer_groups;
   int feature_tile;
   long tangent_chunk;
   int residual_smem;
-  int pad;
+  int pair_unfused;
 } fn_tuning;
 
 fn_status ferminet_get_tuning(const fn_ctx* ctx, fn_tuning* out);

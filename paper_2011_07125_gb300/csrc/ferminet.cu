@@ -300,6 +300,45 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   cudaStream_t s = c->stream;
   const float* P = c->d_params;
   const Geo g = geo_of(c);
+  // Two-electron layers and their spin means in one fused pass (k_pair.cu)
+  // when its kernels cover every layer's shapes; the means of layer l + 1 are
+  // then produced by layer l's two-electron kernel.
+  auto m2_ld = [&](int l) -> long { return tc ? pad64(2 * din2_of(t, l)) : 2L * din2_of(t, l); };
+  bool fused = c->tune.pair_unfused == 0 && pair_layer_supported(n, 4, 4, false, Q, C, m2_ld(0));
+  for (int l = 0; l < L - 1 && fused; ++l)
+    fused = pair_layer_supported(n, din2_of(t, l), d2, true, Q, C, m2_ld(l + 1)) && (l == 0 || din2_of(t, l) == d2);
+  auto pair_means = [&](const float* E, int din, float* m32, __nv_bfloat16* mhi, __nv_bfloat16* mlo, long ldm) {
+    PairArgs pa{};
+    pa.Ein = E;
+    pa.groups = Bc * n;
+    pa.n = n;
+    pa.n_up = t.n_up;
+    pa.C = C;
+    pa.m32 = m32;
+    pa.mhi = mhi;
+    pa.mlo = mlo;
+    pa.ldm = ldm;
+    if (!launch_pair_layer(s, pa, din, din, Q)) c->host_fail = true;
+  };
+  auto pair_layer = [&](int l, const float* E, float* Eout, float* Y2, float* m32, __nv_bfloat16* mhi,
+                        __nv_bfloat16* mlo) {
+    PairArgs pa{};
+    pa.Ein = E;
+    pa.groups = Bc * n;
+    pa.n = n;
+    pa.n_up = t.n_up;
+    pa.C = C;
+    pa.W = P + c->lay.W[l];
+    pa.cb = P + c->lay.c[l];
+    pa.residual = l >= 1 ? 1 : 0;
+    pa.Eout = Eout;
+    pa.Y2 = Y2;
+    pa.m32 = m32;
+    pa.mhi = mhi;
+    pa.mlo = mlo;
+    pa.ldm = m2_ld(l + 1);
+    if (!launch_pair_layer(s, pa, din2_of(t, l), d2, Q)) c->host_fail = true;
+  };
   launch_features(s, x, Bc, w0, n, N, C, Q, g, H0, E0);
   const float* Hc = H0;
   const float* Ec = E0;
@@ -329,7 +368,8 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         } else {
           launch_mean1_bf16(s, Hcb[0], Hcb[1], ldc_b, Bc, n, t.n_up, C, a1, M1b[0], M1b[1], l1);
         }
-        launch_mean2_bf16(s, Ec, Bc, n, t.n_up, Q, a2, C, M2b[0], M2b[1], l2);
+        if (!fused) launch_mean2_bf16(s, Ec, Bc, n, t.n_up, Q, a2, C, M2b[0], M2b[1], l2);
+        else if (l == 0) pair_means(Ec, a2, nullptr, M2b[0], M2b[1], l2);
       }
       {
         Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * d1 * 2.0 * a1);
@@ -427,7 +467,10 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
       if (l < L - 1) {
         float* En = (l % 2 == 0) ? Ea : Eb;
         Prof p2(c, FN_KC_TWO_LAYER, 2.0 * (double)pairs * Q * d2 * a2);
-        launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En, nullptr);
+        if (fused)  // after this layer's GEMMs have read M2b: it now receives layer l + 1's means
+          pair_layer(l, Ec, l + 1 < L - 1 ? En : nullptr, nullptr, nullptr, M2b[0], M2b[1]);
+        else
+          launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En, nullptr);
         Ec = En;
       }
       Hcb[0] = Hnb[0];
@@ -479,7 +522,8 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     {
       Prof pm(c, tangent ? FN_KC_MEANS : FN_KC_COUNT, 0.0);
       launch_mean1(s, Hc, Bc, n, t.n_up, C, a1, M1l);
-      launch_mean2(s, Ec, Bc, n, t.n_up, Q, a2, C, M2l);
+      if (!fused) launch_mean2(s, Ec, Bc, n, t.n_up, Q, a2, C, M2l);
+      else if (l == 0) pair_means(Ec, a2, M2l, nullptr, nullptr, 2L * a2);
     }
     const double fl_rows = 2.0 * (double)Bc * Creal;  // algorithmic rows per walker-column, x2 for FMA
     {
@@ -511,8 +555,12 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     if (l < L - 1) {
       float* En = store ? st->E[l + 1] : ((l % 2 == 0) ? Ea : Eb);
       Prof p2(c, FN_KC_TWO_LAYER, 2.0 * (double)pairs * (tangent ? kQ : 1) * d2 * a2);
-      launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En,
-                       store ? st->Y2[l] : nullptr);
+      if (fused)  // after this layer's GEMMs have read M2: it now receives layer l + 1's means
+        pair_layer(l, Ec, (store || l + 1 < L - 1) ? En : nullptr, store ? st->Y2[l] : nullptr,
+                   store ? st->M2[l + 1] : M2, nullptr, nullptr);
+      else
+        launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En,
+                         store ? st->Y2[l] : nullptr);
       Ec = En;
     }
     Hc = Hn;
@@ -1275,7 +1323,7 @@ fn_status ferminet_get_tuning(const fn_ctx* c, fn_tuning* out) {
 fn_status ferminet_set_tuning(fn_ctx* c, const fn_tuning* t) {
   if (!c || !t) return FN_EINVAL;
   if (t->layer_groups < 0 || t->feature_tile < 0 || t->tangent_chunk < 0 || t->residual_smem < 0 ||
-      t->residual_smem > 1)
+      t->residual_smem > 1 || t->pair_unfused < 0 || t->pair_unfused > 1)
     return fail(c, FN_EINVAL, "bad tuning value");
   if (t->layer_groups > 0 && (t->layer_groups * c->Ct > 256 || (t->layer_groups * c->Ct) % 16))
     return fail(c, FN_EINVAL, "layer_groups gives an invalid tile");

@@ -97,6 +97,26 @@ void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, 
 void launch_two_layer(cudaStream_t s, const float* Ein, long Bc, int n, int Q, int din2, int d2, const float* W,
                       const float* c, bool residual, float* Eout, float* Y2);
 
+// Fused two-electron layer and dense spin means of its output (k_pair.cu).
+// With W null the kernel forms the means of Ein itself.
+struct PairArgs {
+  const float* Ein;     // [groups][n][Q][din] pair rows, 16-byte aligned
+  long groups;          // walkers x electrons
+  int n, n_up, C;       // electrons, spin-up electrons, dense mean columns (1 in a value pass)
+  const float* W;       // [dout][din], or null
+  const float* cb;      // [dout]
+  int residual;         // add the input rows (din == dout)
+  float* Eout;          // [groups][n][Q][dout] new rows, or null when no later kernel reads them
+  float* Y2;            // [groups][n][dout] tanh values (adjoint), or null
+  float* m32;           // dense means [groups][C][ldm] as FP32, or
+  __nv_bfloat16* mhi;   //   as BF16 hi / lo (lo may be null); columns 2 dout .. ldm-1 zero
+  __nv_bfloat16* mlo;
+  long ldm;
+  int tg;               // set by the launcher
+};
+bool pair_layer_supported(int n, int din, int dout, bool layer, int Q, int C, long ldm);
+bool launch_pair_layer(cudaStream_t s, const PairArgs& a, int din, int dout, int Q);
+
 // ---------------------------------------------------------------------------
 // Determinants (k_det.cu)
 struct DetArgs {

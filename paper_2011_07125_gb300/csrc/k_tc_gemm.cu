@@ -38,7 +38,6 @@ constexpr int BM = 128;
 constexpr int BK = 64;            // 64 bf16 = 128 bytes: one swizzle row
 constexpr int STAGES = 4;  // at most; fewer when the residual region needs the space
 constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES_MAX = 256 * BK * 2;
 constexpr int SMEM_BYTES = 227 * 1024;  // dynamic shared memory requested per CTA
 constexpr int BAR_BYTES = 256;
 constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz

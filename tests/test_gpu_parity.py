@@ -289,3 +289,50 @@ def test_step_graph_matches_calls(name, per, prec):
         assert torch.equal(acc, o["accepted"])
         assert torch.equal(e, o["eloc"]) and torch.equal(em, o["emean"])
         assert torch.equal(g, o["grad"])
+
+
+@pytest.mark.parametrize("name,per,prec", [("li", 16, "fp32"), ("ne", 6, "fp32"), ("c4h6", 3, "mixed"),
+                                           ("c4h4x8", 2, "mixed")])
+def test_pair_fused_matches_separate(name, per, prec):
+    """The fused two-electron layer + spin-mean kernel against the separate
+    kernels: same arithmetic in the same order, on the value pass, the
+    local-energy pass and the adjoint (whose forward stores every layer)."""
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P, precision=prec)
+    xx = cuda(x)
+    seeds = torch.linspace(-1.0, 1.0, x.shape[0], device="cuda")
+    res = []
+    for unfused in (0, 1):
+        fn.set_tuning(pair_unfused=unfused)
+        lp = fn.logpsi(xx)[0]
+        out = fn.local_energy(xx)
+        g = fn.logpsi_vjp(xx, seeds)
+        res.append((lp, out["eloc"], out["logpsi"], g))
+        assert fn.sync() == "FN_OK"
+    (lp0, e0, l0, g0), (lp1, e1, l1, g1) = res
+    torch.testing.assert_close(lp0, lp1, rtol=1e-6, atol=1e-6)
+    torch.testing.assert_close(l0, l1, rtol=1e-6, atol=1e-6)
+    torch.testing.assert_close(e0, e1, rtol=1e-4, atol=1e-4)
+    assert float((g0 - g1).norm() / g1.norm()) < 1e-5
+    print(name, prec, "fused vs separate: max |dE|", float((e0 - e1).abs().max()),
+          "bitwise" if torch.equal(e0, e1) and torch.equal(lp0, lp1) else "not bitwise")
+
+
+def test_two_electron_width_outside_fused_kernel():
+    """d2 = 12 is not covered by the fused pair kernel: the separate kernels
+    run, and log|psi| and E_L still match the oracle."""
+    from paper_2011_07125_gb300.binding import FermiNet
+    net = synth.Net(3, 32, 12, 2, 3, 2, 2)
+    geoms = [synth.Geometry(np.array([[0.0, 0.0, -0.8], [0.0, 0.0, 0.8]]), np.array([3.0, 2.0]))]
+    wl = synth.Workload("two-centre", net, geoms, [12], 1.0, 1, 0.02, "fp32", True)
+    P = synth.init_params(oracle.layout(net), seed=3)
+    x = synth.init_walkers(wl, seed=4)
+    fn = FermiNet(net, geoms, counts=[12], precision="fp32")
+    fn.set_params(cuda(P))
+    out = fn.local_energy(cuda(x))
+    ref = oracle.local_energy(net, P, geoms, x)
+    assert fn.sync() == "FN_OK"
+    assert np.all(np.abs(out["logpsi"].cpu().numpy() - ref["logpsi"]) <= logpsi_bound(net, ref))
+    de = np.abs(out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"])
+    bound = eloc_bound(net, ref)
+    assert np.all(de <= bound), (de / bound).max()
