@@ -24,19 +24,20 @@ namespace fn {
 namespace {
 
 constexpr int kPairThreads = 256;
-constexpr int kPairSmemMax = 110 * 1024;  // two blocks per SM
+constexpr int kSmemPerSM = 227 * 1024;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::);
-  asm volatile("cp.async.wait_group 0;\n" ::);
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 __device__ __forceinline__ float comp(const float4& v, int k) {
   return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float4 scale4(const float4& v, float a) {
+  return make_float4(v.x * a, v.y * a, v.z * a, v.w * a);
 }
 
 // Shared-memory pair strides (floats): Q rows of DIN (input) or DO (output)
@@ -45,30 +46,128 @@ template <int DIN, int Q>
 constexpr int in_stride() { return Q * DIN + 4; }
 template <int DO, int Q>
 constexpr int out_stride() { return Q * DO + 4; }
+// Rows per thread task: the Q quantities of one pair, or (value pass) four pairs.
+template <int Q>
+constexpr int task_rows() { return Q == 1 ? 4 : Q; }
+// Resident blocks per SM the kernel is built for (registers and shared memory).
+template <int Q, bool LAYER>
+constexpr int min_blocks() { return LAYER ? (Q == 1 ? 3 : 2) : 4; }
 
 template <int DIN, int DO, int Q, bool LAYER>
 size_t pair_smem_bytes(int n, int tg) {
-  const size_t in = (size_t)tg * n * in_stride<DIN, Q>();
+  // layer: one input tile (refilled while the means of the previous tile are
+  // written) + output tile + weights; means only: two input tiles
+  const size_t in = (size_t)(LAYER ? 1 : 2) * tg * n * in_stride<DIN, Q>();
   const size_t out = LAYER ? (size_t)tg * n * out_stride<DO, Q>() : 0;
   const size_t w = LAYER ? (size_t)DIN * DO + DO : 0;
   const size_t sums = (size_t)tg * 2 * Q * DO;
   return sizeof(float) * (in + out + w + sums);
 }
 
+// Stages the pair rows of groups [g0, g0 + tge) (contiguous in global memory)
+// into a padded shared tile with 16-byte cp.async copies.
+template <int DIN, int Q>
+__device__ __forceinline__ void load_tile(const float* Ein, long g0, int tge, int n, float* dst) {
+  constexpr int IPS = in_stride<DIN, Q>();
+  constexpr int V = Q * DIN / 4;  // float4 per pair
+  const float4* src = reinterpret_cast<const float4*>(Ein + g0 * n * (long)(Q * DIN));
+  const int np = tge * n;
+  for (int t = threadIdx.x; t < np * V; t += kPairThreads) {
+    const int p = t / V, r = t - p * V;
+    cp_async16(dst + p * IPS + 4 * r, src + t);
+  }
+  cp_async_commit();
+}
+
+// Writes the dense mean rows of the tile's groups: 8 columns per thread and
+// step, decided per column quad (a quad never straddles the two spins).
+template <int Q, int ORS, int OPS>
+__device__ __forceinline__ void dense_means(const PairArgs& a, long g0, int tge, const float* sout, const float* sS,
+                                            float inv0, float inv1) {
+  const int n = a.n, n3 = 3 * n;
+  const int cpr = (int)(a.ldm / 8);
+  const int per_group = a.C * cpr;
+  for (int t = threadIdx.x; t < tge * per_group; t += kPairThreads) {
+    const int gq = t / per_group, r = t - gq * per_group;
+    const int c = r / cpr, col0 = (r - c * cpr) * 8;
+    const long G = g0 + gq;
+    const int i = (int)(G % n);
+    // row kind: 0 value, 1 own coordinate (sum), 2 another electron's coordinate, 3 Laplacian, -1 zero
+    int kind = -1, e = 0, q = 0;
+    if (c == 0) {
+      kind = 0;
+    } else if (Q > 1 && c <= n3) {
+      e = (c - 1) / 3;
+      q = 1 + (c - 1) - 3 * e;
+      kind = e == i ? 1 : 2;
+    } else if (Q > 1 && c == n3 + 1) {
+      kind = 3;
+      q = 4;
+    }
+    const float* S = sS + gq * 2 * Q * ORS;
+    float4 v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      v[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int col = col0 + 4 * h;
+      if (kind >= 0 && col < 2 * ORS) {
+        const int s = col / ORS, f = col - s * ORS;
+        const float inv = s == 0 ? inv0 : inv1;
+        if (kind == 2) {
+          if ((e < a.n_up ? 0 : 1) == s)
+            v[h] = scale4(*reinterpret_cast<const float4*>(sout + (gq * n + e) * OPS + q * ORS + f), -inv);
+        } else {
+          v[h] = scale4(*reinterpret_cast<const float4*>(S + (s * Q + q) * ORS + f), inv);
+        }
+      }
+    }
+    const long ob = (G * a.C + c) * a.ldm + col0;
+    if (a.m32) {
+      *reinterpret_cast<float4*>(a.m32 + ob) = v[0];
+      *reinterpret_cast<float4*>(a.m32 + ob + 4) = v[1];
+    } else {
+      const float x[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};
+      __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        hi[jj] = __float2bfloat16_rn(x[jj]);
+        lo[jj] = __float2bfloat16_rn(x[jj] - __bfloat162float(hi[jj]));
+      }
+      *reinterpret_cast<uint4*>(a.mhi + ob) = *reinterpret_cast<const uint4*>(hi);
+      if (a.mlo) *reinterpret_cast<uint4*>(a.mlo + ob) = *reinterpret_cast<const uint4*>(lo);
+    }
+  }
+}
+
+// Per-spin sums of every quantity of the tile's groups (sequential over j).
+template <int Q, int ORS, int OPS>
+__device__ __forceinline__ void spin_sums(const PairArgs& a, int tge, const float* sout, float* sS) {
+  const int n = a.n;
+  for (int t = threadIdx.x; t < tge * 2 * Q * ORS; t += kPairThreads) {
+    const int gq = t / (2 * Q * ORS), r = t - gq * (2 * Q * ORS);
+    const int s = r / (Q * ORS), qf = r - s * (Q * ORS);
+    const int j0 = s == 0 ? 0 : a.n_up, j1 = s == 0 ? a.n_up : n;
+    float acc = 0.f;
+    for (int j = j0; j < j1; ++j) acc += sout[(gq * n + j) * OPS + qf];
+    sS[t] = acc;
+  }
+}
+
 template <int DIN, int DO, int Q, bool LAYER>
-__global__ void __launch_bounds__(kPairThreads, 2) k_pair_layer(PairArgs a) {
+__global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_layer(PairArgs a) {
   static_assert(DIN % 4 == 0 && (DO % 8 == 0 || !LAYER), "feature counts");
   constexpr int IPS = in_stride<DIN, Q>();
   constexpr int OPS = LAYER ? out_stride<DO, Q>() : IPS;
   constexpr int ORS = LAYER ? DO : DIN;  // row stride of one quantity in the output tile
-  constexpr int FG = DO / 8 > 0 ? DO / 8 : 1;
+  constexpr int FG = LAYER ? DO / 8 : 1;
+  constexpr int R = task_rows<Q>();
   extern __shared__ __align__(16) float smem[];
   const int n = a.n, tg = a.tg, tid = threadIdx.x;
-  // [tg n][IPS] input | [tg n][OPS] output (layer) | [DIN][DO] transposed
-  // weights and [DO] bias (layer) | [tg][2][Q][DO] per-spin sums
+  // layer:      [tg n][IPS] input | [tg n][OPS] output | [DIN][DO] weights^T | [DO] bias | [tg][2][Q][DO] sums
+  // means only: 2 x [tg n][IPS] input | [tg][2][Q][DIN] sums
   float* sin = smem;
-  float* after_in = sin + (size_t)tg * n * IPS;
-  float* sout = LAYER ? after_in : sin;
+  float* after_in = sin + (size_t)(LAYER ? 1 : 2) * tg * n * IPS;
+  float* sout_l = after_in;
   float* sW = LAYER ? after_in + (size_t)tg * n * OPS : after_in;
   float* sb = sW + (LAYER ? DIN * DO : 0);
   float* sS = sb + (LAYER ? DO : 0);
@@ -79,57 +178,72 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pair_layer(PairArgs a) {
     }
     for (int t = tid; t < DO; t += kPairThreads) sb[t] = a.cb[t];
   }
+  const float inv0 = a.n_up > 0 ? 1.f / (float)a.n_up : 0.f;
+  const float inv1 = n - a.n_up > 0 ? 1.f / (float)(n - a.n_up) : 0.f;
   const long n_tiles = (a.groups + tg - 1) / tg;
-  const int n3 = 3 * n;
-  for (long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  long tile = blockIdx.x;
+  if (tile < n_tiles) load_tile<DIN, Q>(a.Ein, tile * tg, (int)min((long)tg, a.groups - tile * tg), n, sin);
+  for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
     const long g0 = tile * tg;
     const int tge = (int)min((long)tg, a.groups - g0);
     const int np = tge * n;  // pairs in this tile
-    // stage the input rows: contiguous in global memory, padded per pair here
-    {
-      constexpr int V = Q * DIN / 4;  // float4 per pair
-      const float4* src = reinterpret_cast<const float4*>(a.Ein + g0 * n * (long)(Q * DIN));
-      for (int t = tid; t < np * V; t += kPairThreads) {
-        const int p = t / V, r = t - p * V;
-        cp_async16(sin + p * IPS + 4 * r, src + t);
-      }
-      cp_async_wait_all();
+    const long next = tile + gridDim.x;
+    cp_async_wait_all();
+    __syncthreads();  // this tile's rows are in; every thread is done with the previous tile
+    if (!LAYER) {
+      float* cur = sin + (size_t)(it & 1) * tg * n * IPS;
+      if (next < n_tiles)
+        load_tile<DIN, Q>(a.Ein, next * tg, (int)min((long)tg, a.groups - next * tg), n,
+                          sin + (size_t)((it + 1) & 1) * tg * n * IPS);
+      spin_sums<Q, ORS, OPS>(a, tge, cur, sS);
       __syncthreads();
+      dense_means<Q, ORS, OPS>(a, g0, tge, cur, sS, inv0, inv1);
+      continue;
     }
-    if (LAYER) {
-      for (int task = tid; task < np * FG; task += kPairThreads) {
-        const int p = task / FG, fg = task - p * FG;
-        const float* ip = sin + p * IPS;
-        float acc[Q][8];
+    // ---- the layer: R rows x 8 features per task ----
+    const int nq = Q == 1 ? (np + 3) / 4 : np;  // tasks per feature group
+    for (int task = tid; task < nq * FG; task += kPairThreads) {
+      const int pq = task / FG, fg = task - pq * FG;
+      int prow[R];  // shared offset of each row
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
+      for (int r = 0; r < R; ++r)
+        prow[r] = Q == 1 ? min(pq + r * nq, np - 1) * IPS : pq * IPS + r * DIN;
+      float acc[R][8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[q][j] = 0.f;
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < DIN; k += 4) {
-          float4 xv[Q];
+        for (int j = 0; j < 8; ++j) acc[r][j] = 0.f;
 #pragma unroll
-          for (int q = 0; q < Q; ++q) xv[q] = *reinterpret_cast<const float4*>(ip + q * DIN + k);
+      for (int k = 0; k < DIN; k += 4) {
+        float4 xv[R];
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const float4 w0 = *reinterpret_cast<const float4*>(sW + (k + kk) * DO + fg * 8);
-            const float4 w1 = *reinterpret_cast<const float4*>(sW + (k + kk) * DO + fg * 8 + 4);
-            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        for (int r = 0; r < R; ++r) xv[r] = *reinterpret_cast<const float4*>(sin + prow[r] + k);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              const float xq = comp(xv[q], kk);
+        for (int kk = 0; kk < 4; ++kk) {
+          const float4 w0 = *reinterpret_cast<const float4*>(sW + (k + kk) * DO + fg * 8);
+          const float4 w1 = *reinterpret_cast<const float4*>(sW + (k + kk) * DO + fg * 8 + 4);
+          const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-              for (int j = 0; j < 8; ++j) acc[q][j] = fmaf(wv[j], xq, acc[q][j]);
-            }
+          for (int r = 0; r < R; ++r) {
+            const float xr = comp(xv[r], kk);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[r][j] = fmaf(wv[j], xr, acc[r][j]);
           }
         }
-        // forward-Laplacian tanh, residual, stores
-        float ov[Q][8];
-        float yv[8];
+      }
+      // forward-Laplacian tanh, residual, stores (shared output tile, new rows, tanh values)
+      const int npair = Q == 1 ? R : 1;
+#pragma unroll
+      for (int u = 0; u < npair; ++u) {
+        const int p = Q == 1 ? pq + u * nq : pq;
+        if (p >= np) break;
+        const float* ip = sin + p * IPS;
+        float ov[Q][8], yv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int f = fg * 8 + j;
-          const float y = tanhf(acc[0][j] + sb[f]);
+          const float z0 = Q == 1 ? acc[u][j] : acc[0][j];
+          const float y = tanhf(z0 + sb[f]);
           const float s = 1.f - y * y;
           yv[j] = y;
           ov[0][j] = y + (a.residual ? ip[f] : 0.f);
@@ -145,7 +259,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pair_layer(PairArgs a) {
         for (int q = 0; q < Q; ++q) {
           const float4 o0 = make_float4(ov[q][0], ov[q][1], ov[q][2], ov[q][3]);
           const float4 o1 = make_float4(ov[q][4], ov[q][5], ov[q][6], ov[q][7]);
-          float* so = sout + p * OPS + q * DO + fg * 8;
+          float* so = sout_l + p * OPS + q * DO + fg * 8;
           *reinterpret_cast<float4*>(so) = o0;
           *reinterpret_cast<float4*>(so + 4) = o1;
           if (a.Eout) {
@@ -160,94 +274,40 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pair_layer(PairArgs a) {
           *reinterpret_cast<float4*>(gy + 4) = make_float4(yv[4], yv[5], yv[6], yv[7]);
         }
       }
-      __syncthreads();
     }
-    // per-spin sums of every quantity (sequential over j, as the plain definition)
-    for (int t = tid; t < tge * 2 * Q * ORS; t += kPairThreads) {
-      const int gq = t / (2 * Q * ORS), r = t - gq * (2 * Q * ORS);
-      const int s = r / (Q * ORS), qf = r - s * (Q * ORS);
-      const int q = qf / ORS, f = qf - q * ORS;
-      const int j0 = s == 0 ? 0 : a.n_up, j1 = s == 0 ? a.n_up : n;
-      float acc = 0.f;
-      for (int j = j0; j < j1; ++j) acc += sout[(gq * n + j) * OPS + q * ORS + f];
-      sS[t] = acc;
-    }
+    __syncthreads();  // output tile complete; the input tile is free
+    if (next < n_tiles) load_tile<DIN, Q>(a.Ein, next * tg, (int)min((long)tg, a.groups - next * tg), n, sin);
+    spin_sums<Q, ORS, OPS>(a, tge, sout_l, sS);
     __syncthreads();
-    // dense mean rows, 8 columns per thread and step
-    {
-      const int cpr = (int)(a.ldm / 8);
-      const int per_group = a.C * cpr;
-      for (int t = tid; t < tge * per_group; t += kPairThreads) {
-        const int gq = t / per_group, r = t - gq * per_group;
-        const int c = r / cpr, col0 = (r - c * cpr) * 8;
-        const long G = g0 + gq;
-        const int i = (int)(G % n);
-        const float* S = sS + gq * 2 * Q * ORS;
-        int e = -1, dd = 0;
-        if (Q > 1 && c >= 1 && c <= n3) {
-          e = (c - 1) / 3;
-          dd = (c - 1) - 3 * e;
-        }
-        float v[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int col = col0 + jj;
-          float x = 0.f;
-          if (col < 2 * ORS) {
-            const int s = col / ORS, f = col - s * ORS;
-            const int j0 = s == 0 ? 0 : a.n_up, j1 = s == 0 ? a.n_up : n;
-            const int ns = j1 - j0;
-            if (ns > 0) {
-              const float inv = 1.f / (float)ns;
-              if (c == 0) {
-                x = S[(s * Q) * ORS + f] * inv;
-              } else if (e >= 0) {
-                if (e == i) x = S[(s * Q + 1 + dd) * ORS + f] * inv;
-                else if (e >= j0 && e < j1) x = -sout[(gq * n + e) * OPS + (1 + dd) * ORS + f] * inv;
-              } else if (Q > 1 && c == n3 + 1) {
-                x = S[(s * Q + 4) * ORS + f] * inv;
-              }
-            }
-          }
-          v[jj] = x;
-        }
-        const long ob = (G * a.C + c) * (long)a.ldm + col0;
-        if (a.m32) {
-          *reinterpret_cast<float4*>(a.m32 + ob) = make_float4(v[0], v[1], v[2], v[3]);
-          *reinterpret_cast<float4*>(a.m32 + ob + 4) = make_float4(v[4], v[5], v[6], v[7]);
-        } else {
-          __align__(16) __nv_bfloat16 h[8], lo[8];
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            h[jj] = __float2bfloat16_rn(v[jj]);
-            lo[jj] = __float2bfloat16_rn(v[jj] - __bfloat162float(h[jj]));
-          }
-          *reinterpret_cast<uint4*>(a.mhi + ob) = *reinterpret_cast<const uint4*>(h);
-          if (a.mlo) *reinterpret_cast<uint4*>(a.mlo + ob) = *reinterpret_cast<const uint4*>(lo);
-        }
-      }
-    }
-    __syncthreads();  // the tiles are refilled next
+    dense_means<Q, ORS, OPS>(a, g0, tge, sout_l, sS, inv0, inv1);
   }
+  cp_async_wait_all();  // no copy outlives the block
 }
 
 template <int DIN, int DO, int Q, bool LAYER>
 void launch_inst(cudaStream_t s, PairArgs a) {
+  auto kern = k_pair_layer<DIN, DO, Q, LAYER>;
+  constexpr int MB = min_blocks<Q, LAYER>();
+  const size_t budget = kSmemPerSM / MB - 1024;
   static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(k_pair_layer<DIN, DO, Q, LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemMax);
-  });
-  // groups per tile: about two tasks (or output steps) per thread, within the
-  // shared-memory budget of two blocks per SM
-  const int per_group = LAYER ? a.n * (DO / 8) : a.C * (int)(a.ldm / 8);
-  int tg = (2 * kPairThreads + per_group - 1) / per_group;
+  std::call_once(once, [&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget); });
+  // groups per tile: about one task (layer) or two output steps (means) per
+  // thread, within the shared-memory share of the resident blocks
+  const int per_group = LAYER ? (a.n * (DO / 8) + (Q == 1 ? 3 : 0)) / (Q == 1 ? 4 : 1) : a.C * (int)(a.ldm / 8);
+  const int target = LAYER ? kPairThreads : 2 * kPairThreads;
+  int tg = (target + per_group - 1) / per_group;
   if (tg < 1) tg = 1;
-  while (tg > 1 && pair_smem_bytes<DIN, DO, Q, LAYER>(a.n, tg) > (size_t)kPairSmemMax) --tg;
+  while (tg > 1 && pair_smem_bytes<DIN, DO, Q, LAYER>(a.n, tg) > budget) --tg;
   a.tg = tg;
   const size_t smem = pair_smem_bytes<DIN, DO, Q, LAYER>(a.n, tg);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPairThreads, smem) != cudaSuccess || occ < 1) occ = 1;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long tiles = (a.groups + tg - 1) / tg;
-  const long blocks = std::min<long>(tiles, 152L * 2);  // persistent: two blocks per SM
-  FN_COUNT(1), k_pair_layer<DIN, DO, Q, LAYER><<<(unsigned)blocks, kPairThreads, smem, s>>>(a);
+  const long blocks = std::min<long>(tiles, (long)sms * occ);  // persistent
+  FN_COUNT(1), kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(a);
 }
 
 template <int Q>
@@ -278,10 +338,11 @@ bool pair_layer_supported(int n, int din, int dout, bool layer, int Q, int C, lo
   const int d = layer ? dout : din;
   if (!(din_ok && dout_ok && (Q == 1 || Q == kQ) && ldm % 8 == 0 && ldm >= 2 * d && C >= 1)) return false;
   if (Q == kQ && C < 3 * n + 2) return false;
-  // one group per tile must fit
-  const size_t in = (size_t)n * (Q * din + 4), out = layer ? (size_t)n * (Q * dout + 4) : 0;
+  // one group per tile must fit in the shared-memory share of a block
+  const int mb = layer ? (Q == 1 ? 3 : 2) : 4;
+  const size_t in = (size_t)(layer ? 1 : 2) * n * (Q * din + 4), out = layer ? (size_t)n * (Q * dout + 4) : 0;
   const size_t w = layer ? (size_t)din * dout + dout : 0;
-  return sizeof(float) * (in + out + w + 2 * Q * d) <= (size_t)kPairSmemMax;
+  return sizeof(float) * (in + out + w + 2 * Q * d) <= (size_t)(kSmemPerSM / mb - 1024);
 }
 
 bool launch_pair_layer(cudaStream_t s, const PairArgs& a, int din, int dout, int Q) {
