@@ -24,8 +24,9 @@ __device__ __forceinline__ int geo_of(const Geo& g, long wg) { return g.geo ? g.
 // Gauss-Jordan inversion of an n x n matrix (n <= NM <= 32) held one row per
 // lane in a[]; b[] starts as the identity row of the lane and ends as the row
 // of A^-1.  Lanes n..NM-1 hold identity padding rows.  All lanes end with the
-// same logabs, sign and pivot extremes.
-template <int NM, class T, int WIDTH = 32>
+// same logabs, sign and pivot extremes.  With INV false b[] is left alone
+// (the determinant alone: no inverse rows are swapped or eliminated).
+template <int NM, class T, int WIDTH = 32, bool INV = true>
 __device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane, T& logabs, T& sgn, T& pmin,
                                         T& pmax, bool& sing, int nreal = 1 << 30) {
   logabs = T(0);
@@ -53,8 +54,8 @@ __device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane,
       const int src = lane == k ? p : (lane == p ? k : lane);
 #pragma unroll
       for (int c = 0; c < NM; ++c) {
-        a[c] = __shfl_sync(FULL, a[c], src, WIDTH);
-        b[c] = __shfl_sync(FULL, b[c], src, WIDTH);
+        if (c >= k) a[c] = __shfl_sync(FULL, a[c], src, WIDTH);  // columns < k are eliminated
+        if (INV) b[c] = __shfl_sync(FULL, b[c], src, WIDTH);
       }
       if (p != k) sgn = -sgn;
     }
@@ -80,8 +81,10 @@ __device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane,
         T rk = __shfl_sync(FULL, a[c], k, WIDTH) * iu;
         a[c] = (lane == k) ? rk : fma(-fct, rk, a[c]);
       }
-      T rb = __shfl_sync(FULL, b[c], k, WIDTH) * iu;
-      b[c] = (lane == k) ? rb : fma(-fct, rb, b[c]);
+      if (INV) {
+        T rb = __shfl_sync(FULL, b[c], k, WIDTH) * iu;
+        b[c] = (lane == k) ? rb : fma(-fct, rb, b[c]);
+      }
     }
   }
 }
@@ -232,7 +235,10 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
   }
   T logabs, sgn, pmin, pmax;
   bool sing;
-  warp_gj<NM, T, 16>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
+  if (a.minv)
+    warp_gj<NM, T, 16, true>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
+  else
+    warp_gj<NM, T, 16, false>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
   const bool flag = !sing && pmin < (T)a.pivot_tau * pmax;
   if (sl == 0) {
     a.logdet[mat] = sing ? -INFINITY : (float)logabs;

@@ -174,6 +174,67 @@ __global__ void __launch_bounds__(256) k_mean1_rows(const float* __restrict__ h3
   }
 }
 
+// Same spin means with 16-byte accesses: one thread per 8 output columns of a
+// (walker, column c) row, loading 8 features of every electron of its spin
+// (all loads independent).  din and the row strides are multiples of 8; the
+// sum runs over i in order and is divided by the count, as k_mean1_rows.
+template <bool BF>
+__global__ void __launch_bounds__(256) k_mean1_vec(const float* __restrict__ h32,
+                                                   const __nv_bfloat16* __restrict__ hhi,
+                                                   const __nv_bfloat16* __restrict__ hlo, int ldin, long rows,
+                                                   int n, int n_up, int C, int din, float* __restrict__ out32,
+                                                   __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo,
+                                                   int ldout) {
+  const int cpr = ldout / 8;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * cpr) return;
+  const long wc = t / cpr;
+  const int col0 = (int)(t - wc * cpr) * 8;
+  const long w = wc / C;
+  const int c = (int)(wc - w * C);
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (col0 < 2 * din) {
+    const int s = col0 / din, f0 = col0 - s * din;
+    const int i0 = s == 0 ? 0 : n_up, i1 = s == 0 ? n_up : n;
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 5
+    for (int i = i0; i < i1; ++i) {
+      const long r = ((w * n + i) * (long)C + c) * ldin + f0;
+      if (BF) {
+        const uint4 hv = *reinterpret_cast<const uint4*>(hhi + r);
+        const uint4 lv = hlo ? *reinterpret_cast<const uint4*>(hlo + r) : make_uint4(0u, 0u, 0u, 0u);
+        const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&hv);
+        const __nv_bfloat16* lb = reinterpret_cast<const __nv_bfloat16*>(&lv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] += __bfloat162float(hb[j]) + __bfloat162float(lb[j]);
+      } else {
+        const float4 x0 = *reinterpret_cast<const float4*>(h32 + r);
+        const float4 x1 = *reinterpret_cast<const float4*>(h32 + r + 4);
+        a[0] += x0.x; a[1] += x0.y; a[2] += x0.z; a[3] += x0.w;
+        a[4] += x1.x; a[5] += x1.y; a[6] += x1.z; a[7] += x1.w;
+      }
+    }
+    if (i1 > i0) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = a[j] / (float)(i1 - i0);
+    }
+  }
+  const long ob = wc * ldout + col0;
+  if (out32) {
+    *reinterpret_cast<float4*>(out32 + ob) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(out32 + ob + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      hi[j] = __float2bfloat16_rn(v[j]);
+      lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+    }
+    *reinterpret_cast<uint4*>(ohi + ob) = *reinterpret_cast<const uint4*>(hi);
+    if (olo) *reinterpret_cast<uint4*>(olo + ob) = *reinterpret_cast<const uint4*>(lo);
+  }
+}
+
 __global__ void k_split_bf16(const float* __restrict__ src, long src_ld, long rows, long cols,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long dst_ld) {
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,6 +356,12 @@ void launch_features(cudaStream_t s, const float* x, long Bc, long w0, int n, in
 
 void launch_mean1(cudaStream_t s, const float* H, long Bc, int n, int n_up, int C, int din, float* M1) {
   if (Bc * C <= 0) return;
+  if (din % 8 == 0) {
+    const long tot = Bc * C * (2L * din / 8);
+    FN_COUNT(1), k_mean1_vec<false><<<nblk(tot, 256), 256, 0, s>>>(H, nullptr, nullptr, din, Bc * C, n, n_up, C, din,
+                                                                   M1, nullptr, nullptr, 2 * din);
+    return;
+  }
   FN_COUNT(1), k_mean1_rows<<<(unsigned)(Bc * C), 256, 0, s>>>(H, nullptr, nullptr, din, n, n_up, C, din, M1, nullptr,
                                                                nullptr, 2 * din);
 }
@@ -318,6 +385,12 @@ void launch_mean2_bf16(cudaStream_t s, const float* E, long Bc, int n, int n_up,
 void launch_mean1_bf16(cudaStream_t s, const __nv_bfloat16* hi, const __nv_bfloat16* lo, long ldin, long Bc, int n,
                        int n_up, int C, int din, __nv_bfloat16* ohi, __nv_bfloat16* olo, long ldout) {
   if (Bc * C <= 0) return;
+  if (din % 8 == 0 && ldin % 8 == 0 && ldout % 8 == 0) {
+    const long tot = Bc * C * (ldout / 8);
+    FN_COUNT(1), k_mean1_vec<true><<<nblk(tot, 256), 256, 0, s>>>(nullptr, hi, lo, (int)ldin, Bc * C, n, n_up, C, din,
+                                                                  nullptr, ohi, olo, (int)ldout);
+    return;
+  }
   FN_COUNT(1), k_mean1_rows<<<(unsigned)(Bc * C), 256, 0, s>>>(nullptr, hi, lo, (int)ldin, n, n_up, C, din, nullptr, ohi,
                                                                olo, (int)ldout);
 }
