@@ -288,6 +288,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   float* sgn = ar.get<float>(Bc * K * 2);
   float* dgrad = tangent ? ar.get<float>(Bc * K * 2 * 3 * n) : nullptr;
   float* dlap = tangent ? ar.get<float>(Bc * K * 2) : nullptr;
+  unsigned char* redo = tangent ? ar.get<unsigned char>(Bc * K * 2) : nullptr;
   const long nss = (long)c->ns_max * c->ns_max;
   if (store) {
     st->O = O;
@@ -601,6 +602,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   da.pivot_tau = c->pivot_tau;
   da.force64 = c->force64;
   da.nss = nss;
+  da.redo = redo;
   {
     double fl = 0.0;
     for (int sp = 0; sp < 2; ++sp) {

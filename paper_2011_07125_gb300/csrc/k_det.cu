@@ -296,23 +296,42 @@ __global__ void __launch_bounds__(128) k_det_value_pair(DetArgs a) {
   }
 }
 
+// Coordinates handled together in the tangent pass: NM threads per coordinate.
+template <int NM>
+constexpr int coord_batch() { return 128 / NM; }
+
 template <int NM, class T>
 struct TangentSmem {
-  T Ms[NM][NM + 1];
-  T Os[NM][NM + 1];
-  T Es[NM][NM + 1];
+  T Ms[NM][NM];        // A^-1, zero padded
+  T Os[NM][NM + 1];    // orbital values o_i(r_j)
+  T Es[NM][NM + 1];    // envelopes e_i(r_j)
   T Eg[3][NM][NM + 1];
   T El[NM][NM + 1];
-  T Xs[128 * NM];
-  T Tr[128];   // [cb][ns] diagonal entries of X_c
-  T Tr2[128];  // [cb][ns] row i of X_c times column i of X_c
+  // rows padded to NM + 1: the threads of a coordinate read one row each
+  T ET[NM][NM + 1];        // Es transposed [j][i], zero padded
+  T OT[NM][NM + 1];        // Os transposed
+  T EgT[3][NM][NM + 1];    // Eg transposed
+  float Draw[2][coord_batch<NM>()][NM][NM + 1];  // d o_i(r_j) / d x_c as [c][j][i], two buffers
+  T Xs[coord_batch<NM>()][NM * (NM + 1)];        // X_c = A^-1 d_c A, column j at j (NM + 1)
 };
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
 
 // Tangent-pass body for one matrix in precision T (128 threads).  Returns
 // whether the pivot ratio flags the matrix (block-uniform).
+//
+// d log|det A| / d x_c = tr(X_c) and lap log|det A| = tr(A^-1 lap A) -
+// sum_c tr(X_c^2) with X_c = A^-1 d_c A, where A_ij = o_i(r_j) e_i(r_j) and
+// d_c A_ij = (d_c o_i(r_j)) e_i(r_j) + [c is a coordinate of electron j]
+// o_i(r_j) d_c e_i(r_j).  The orbital tangents of a batch of coordinates are
+// copied into shared memory while the previous batch is reduced.
 template <int NM, class T>
 __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, const float* R, char* raw,
                                  bool count) {
+  constexpr int CB = coord_batch<NM>();
   TangentSmem<NM, T>& sm = *reinterpret_cast<TangentSmem<NM, T>*>(raw);
   __shared__ double red[4];
   __shared__ int sing_s, flag_s;
@@ -322,16 +341,46 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
   auto orow = [&](int jg, int c) -> const float* {
     return a.O + ((m.w * a.n + jg) * (long)a.C + c) * a.ldo + m.q0;
   };
+  // zero padding of the transposed tiles and of both raw buffers (the copies
+  // below only ever write entries i, j < ns)
+  for (int t = tid; t < NM * (NM + 1); t += 128) {
+    (&sm.ET[0][0])[t] = T(0);
+    (&sm.OT[0][0])[t] = T(0);
+    (&sm.EgT[0][0][0])[t] = T(0);
+    (&sm.EgT[1][0][0])[t] = T(0);
+    (&sm.EgT[2][0][0])[t] = T(0);
+  }
+  for (int t = tid; t < 2 * CB * NM * (NM + 1); t += 128) (&sm.Draw[0][0][0][0])[t] = 0.f;
+  __syncthreads();
+  const int nb = (n3 + CB - 1) / CB;
+  auto stage = [&](int b) {  // raw tangents of batch b: one (coordinate, electron) run per thread
+    if (tid < CB * ns) {
+      const int cl = tid / ns, j = tid - cl * ns, c = b * CB + cl;
+      if (c < n3) {
+        const float* src = orow(m.j0 + j, 1 + c);
+        float* dst = &sm.Draw[b & 1][cl][j][0];
+        for (int i = 0; i < ns; ++i) cp_async4(dst + i, src + i);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  stage(0);
   for (int t = tid; t < ns * ns; t += 128) {
     int i = t / ns, j = t % ns;
     T ev, eg[3], el;
     envelope<T>(a, m, i, m.j0 + j, R, ev, eg, el, true);
+    const T o = (T)orow(m.j0 + j, 0)[i];
     sm.Es[i][j] = ev;
     sm.Eg[0][i][j] = eg[0];
     sm.Eg[1][i][j] = eg[1];
     sm.Eg[2][i][j] = eg[2];
     sm.El[i][j] = el;
-    sm.Os[i][j] = (T)orow(m.j0 + j, 0)[i];
+    sm.Os[i][j] = o;
+    sm.ET[j][i] = ev;
+    sm.OT[j][i] = o;
+    sm.EgT[0][j][i] = eg[0];
+    sm.EgT[1][j][i] = eg[1];
+    sm.EgT[2][j][i] = eg[2];
   }
   __syncthreads();
   if (warp == 0) {
@@ -349,10 +398,9 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
     T logabs, sgn, pmin, pmax;
     bool sing;
     warp_gj<NM, T>(ra, rb, ns, lane, logabs, sgn, pmin, pmax, sing);
-    if (lane < ns) {
+    if (lane < NM) {
 #pragma unroll
-      for (int c = 0; c < NM; ++c)
-        if (c < ns) sm.Ms[lane][c] = rb[c];
+      for (int c = 0; c < NM; ++c) sm.Ms[lane][c] = (lane < ns && c < ns) ? rb[c] : T(0);
     }
     if (lane == 0) {
       const bool flag = !sing && pmin < (T)a.pivot_tau * pmax;
@@ -369,8 +417,10 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
   __syncthreads();
   const bool flag = flag_s != 0;
   if (sing_s) {
+    asm volatile("cp.async.wait_group 0;\n" ::);
     if (tid == 0) a.dlap[mat] = 0.f;
     for (int c = tid; c < n3; c += 128) a.dgrad[mat * n3 + c] = 0.f;
+    __syncthreads();
     return false;
   }
   // tr(A^-1 lap A), lap A_ij = lap o e + o lap e + 2 grad_j o . grad_j e
@@ -383,55 +433,56 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
     T la = lo * sm.Es[i][j] + sm.Os[i][j] * sm.El[i][j] + T(2) * cross;
     part += (double)(sm.Ms[j][i] * la);
   }
-  // coordinates in batches of cb: X_c = A^-1 d_c A, column j per thread
-  const int cb = 128 / ns;
-  for (int c0 = 0; c0 < n3; c0 += cb) {
-    const int cl = tid / ns, j = tid % ns, c = c0 + cl;
-    if (cl < cb && c < n3) {
-      const int jg = m.j0 + j, e = c / 3, dd = c % 3;
-      const float* od = orow(jg, 1 + c);
-      T col[NM];
+  // coordinates in batches of CB: thread (cl, j) forms column j of X_c
+  const int cl = tid / NM, j = tid % NM;
+  for (int b = 0; b < nb; ++b) {
+    if (b + 1 < nb) {
+      stage(b + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    __syncthreads();  // batch b's tangents are visible to every thread
+    const int c = b * CB + cl;
+    const bool act = c < n3;
+    T x[NM];
+    if (act) {
+      const int e = c / 3, dd = c - 3 * e;
+      const bool own = e == m.j0 + j && j < ns;
+      const float* rw = &sm.Draw[b & 1][cl][j][0];
+      T d[NM];
+#pragma unroll
+      for (int l = 0; l < NM; ++l) {
+        const T v = (T)rw[l] * sm.ET[j][l];
+        d[l] = own ? fma(sm.OT[j][l], sm.EgT[dd][j][l], v) : v;
+      }
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
-        if (i < ns) {
-          T v = (T)od[i] * sm.Es[i][j];
-          if (e == jg) v = fma(sm.Os[i][j], sm.Eg[dd][i][j], v);
-          col[i] = v;
-        } else {
-          col[i] = T(0);
-        }
-      }
-      T* X = sm.Xs + (long)cl * ns * ns;
-      for (int i = 0; i < ns; ++i) {
         T acc = T(0);
 #pragma unroll
-        for (int l = 0; l < NM; ++l)
-          if (l < ns) acc = fma(sm.Ms[i][l], col[l], acc);
-        X[i * ns + j] = acc;
+        for (int l = 0; l < NM; ++l) acc = fma(sm.Ms[i][l], d[l], acc);
+        x[i] = acc;
       }
+#pragma unroll
+      for (int i = 0; i < NM; ++i) sm.Xs[cl][j * (NM + 1) + i] = x[i];
     }
-    __syncthreads();
-    // traces, one thread per (coordinate, row i): row i of X_c against column
-    // i, then a reduction over i inside each coordinate's group of threads
-    if (cl < cb && c < n3) {
-      const T* X = sm.Xs + (long)cl * ns * ns;
-      const int i = j;  // thread (cl, j) takes row i = j
-      T r2 = T(0);
-      for (int j2 = 0; j2 < ns; ++j2) r2 = fma(X[i * ns + j2], X[j2 * ns + i], r2);
-      sm.Tr[cl * ns + i] = X[i * ns + i];  // index = thread id < cb * ns <= 128
-      sm.Tr2[cl * ns + i] = r2;
+    __syncwarp();
+    T tr = T(0), tr2 = T(0);
+    if (act) {
+      tr = sm.Xs[cl][j * (NM + 1) + j];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) tr2 = fma(x[i], sm.Xs[cl][i * (NM + 1) + j], tr2);  // X_ij X_ji
     }
-    __syncthreads();
-    if (tid < cb && c0 + tid < n3) {
-      T tr = T(0), tr2 = T(0);
-      for (int i = 0; i < ns; ++i) {
-        tr += sm.Tr[tid * ns + i];
-        tr2 += sm.Tr2[tid * ns + i];
-      }
-      a.dgrad[mat * n3 + c0 + tid] = (float)tr;
+#pragma unroll
+    for (int off = NM / 2; off > 0; off >>= 1) {
+      tr += __shfl_xor_sync(FULL, tr, off, NM < 32 ? NM : 32);
+      tr2 += __shfl_xor_sync(FULL, tr2, off, NM < 32 ? NM : 32);
+    }
+    if (act && j == 0) {
+      a.dgrad[mat * n3 + c] = (float)tr;
       part -= (double)tr2;
     }
-    __syncthreads();
+    __syncthreads();  // Draw[b & 1] and Xs are refilled next
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
@@ -442,8 +493,9 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
   return flag;
 }
 
-// Tangent pass: one 128-thread block per matrix; FP64 redo of matrices whose
-// FP32 pivot ratio falls below pivot_tau.
+// Tangent pass: one 128-thread block per matrix in FP32.  A matrix whose FP32
+// pivot ratio falls below pivot_tau is marked in a.redo and done again in
+// FP64 by k_det_tangent_redo.
 template <int NM>
 __global__ void __launch_bounds__(128) k_det_tangent(DetArgs a) {
   extern __shared__ __align__(16) char raw[];
@@ -455,13 +507,24 @@ __global__ void __launch_bounds__(128) k_det_tangent(DetArgs a) {
       a.logdet[mat] = 0.f;
       a.sign[mat] = 1.f;
       a.dlap[mat] = 0.f;
+      a.redo[mat] = 0;
     }
     for (int c = tid; c < n3; c += 128) a.dgrad[mat * n3 + c] = 0.f;
     return;
   }
   const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
   const bool flag = det_tangent_body<NM, float>(a, mat, m, R, raw, true);
-  if (flag || a.force64) det_tangent_body<NM, double>(a, mat, m, R, raw, false);
+  if (tid == 0) a.redo[mat] = (flag || a.force64) ? 1 : 0;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(128) k_det_tangent_redo(DetArgs a) {
+  extern __shared__ __align__(16) char raw[];
+  const long mat = blockIdx.x;
+  if (!a.redo[mat]) return;  // block-uniform
+  const MatId m = mat_id(mat, a);
+  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
+  det_tangent_body<NM, double>(a, mat, m, R, raw, false);
 }
 
 template <int NM>
@@ -469,13 +532,16 @@ void launch_nm(cudaStream_t s, const DetArgs& a) {
   long nmat = a.Bc * a.K * 2;
   if (nmat <= 0) return;
   if (a.tangent) {
-    const int smem = (int)sizeof(TangentSmem<NM, double>);
+    const int smem = (int)sizeof(TangentSmem<NM, float>);
+    const int smem64 = (int)sizeof(TangentSmem<NM, double>);
     static bool attr = false;  // set once per process (the attribute is per function)
     if (!attr) {
       cudaFuncSetAttribute(k_det_tangent<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaFuncSetAttribute(k_det_tangent_redo<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
       attr = true;
     }
     FN_COUNT(1), k_det_tangent<NM><<<(unsigned)nmat, 128, smem, s>>>(a);
+    FN_COUNT(1), k_det_tangent_redo<NM><<<(unsigned)nmat, 128, smem64, s>>>(a);
   } else if (NM <= 16 && (long)a.n * a.N * 4 * sizeof(float) <= 32768) {
     const long npair = a.Bc * a.K;
     FN_COUNT(1), k_det_value_pair<NM <= 16 ? NM : 16><<<(unsigned)((npair + 3) / 4), 128,

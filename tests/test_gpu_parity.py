@@ -336,3 +336,38 @@ def test_two_electron_width_outside_fused_kernel():
     de = np.abs(out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"])
     bound = eloc_bound(net, ref)
     assert np.all(de <= bound), (de / bound).max()
+
+
+@pytest.mark.parametrize("env", [{"FERMINET_PIVOT_TAU": "0.999"}, {"FERMINET_DET64": "1"}])
+def test_fp64_determinant_redo(monkeypatch, env):
+    """Every orbital matrix goes through the FP64 redo of the tangent pass
+    (flagged by the pivot ratio, or forced): E_L still matches the oracle,
+    and the flagged count reports the matrices when flagging is by ratio."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    wl, lay, P, x, geo = setup("c4h6", 3)
+    fn = make(wl, P)
+    out = fn.local_energy(cuda(x))
+    assert fn.sync() == "FN_OK"
+    ref = oracle.local_energy(wl.net, P, wl.geoms, x, geo=geo)
+    de = np.abs(out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"])
+    bound = eloc_bound(wl.net, ref)
+    assert np.all(de <= bound), (de / bound).max()
+    assert np.all(np.abs(out["logpsi"].cpu().numpy() - ref["logpsi"]) <= logpsi_bound(wl.net, ref))
+    if "FERMINET_PIVOT_TAU" in env:
+        fn.local_energy(cuda(x))
+        assert fn.flagged_matrices() > 0
+
+
+def test_singular_walker_in_tangent_pass():
+    """The singular walker of the value-pass test, through the local-energy
+    pass: status FN_ESINGULAR, log|psi| = -inf there, the others finite."""
+    wl, lay, P, x, geo = setup("li", 4)
+    x = x.copy()
+    x[1, 1] = x[1, 0]
+    fn = make(wl, P)
+    out = fn.local_energy(cuda(x))
+    assert fn.sync() == "FN_ESINGULAR"
+    lp = out["logpsi"].cpu().numpy()
+    assert np.isneginf(lp[1])
+    assert np.all(np.isfinite(out["eloc"].cpu().numpy()[[0, 2, 3]]))
