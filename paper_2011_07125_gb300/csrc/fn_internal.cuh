@@ -140,7 +140,7 @@ struct DetArgs {
   float pivot_tau;
   long nss;            // stride between stored matrices (ns_max^2)
   int force64;         // redo every matrix in FP64 (diagnostics)
-  unsigned char* redo; // [Bc][K][2] FP64 redo marks (tangent pass)
+  int* redo;           // [1 + Bc K 2]: count, then the matrices to redo in FP64 (tangent pass)
 };
 void launch_det(cudaStream_t s, const DetArgs& a);
 

@@ -353,14 +353,17 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
   for (int t = tid; t < 2 * CB * NM * (NM + 1); t += 128) (&sm.Draw[0][0][0][0])[t] = 0.f;
   __syncthreads();
   const int nb = (n3 + CB - 1) / CB;
-  auto stage = [&](int b) {  // raw tangents of batch b: one (coordinate, electron) run per thread
-    if (tid < CB * ns) {
-      const int cl = tid / ns, j = tid - cl * ns, c = b * CB + cl;
-      if (c < n3) {
-        const float* src = orow(m.j0 + j, 1 + c);
-        float* dst = &sm.Draw[b & 1][cl][j][0];
-        for (int i = 0; i < ns; ++i) cp_async4(dst + i, src + i);
-      }
+  // raw tangents of batch b: the NM lanes of a run slot copy consecutive
+  // orbitals i of one (coordinate, electron) run
+  const int li = tid % NM, slot = tid / NM;
+  const float* obase = a.O + (m.w * a.n + m.j0) * (long)a.C * a.ldo + m.q0 + li;
+  const int ldo_i = (int)a.ldo;
+  auto stage = [&](int b) {
+#pragma unroll 1
+    for (int r = slot; r < CB * NM; r += 128 / NM) {
+      const int cl = r / NM, j = r % NM, c = b * CB + cl;
+      if (j < ns && li < ns && c < n3)
+        cp_async4(&sm.Draw[b & 1][cl][j][li], obase + (long)((j * a.C + 1 + c) * ldo_i));
     }
     asm volatile("cp.async.commit_group;\n" ::);
   };
@@ -460,7 +463,7 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
       for (int i = 0; i < NM; ++i) {
         T acc = T(0);
 #pragma unroll
-        for (int l = 0; l < NM; ++l) acc = fma(sm.Ms[i][l], d[l], acc);
+        for (int l = 0; l < NM; ++l) acc = fma(sm.Ms[i][l], d[l], acc);  // row i: a broadcast read
         x[i] = acc;
       }
 #pragma unroll
@@ -494,10 +497,13 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
 }
 
 // Tangent pass: one 128-thread block per matrix in FP32.  A matrix whose FP32
-// pivot ratio falls below pivot_tau is marked in a.redo and done again in
-// FP64 by k_det_tangent_redo.
+// pivot ratio falls below pivot_tau is appended to the list a.redo and done
+// again in FP64 by k_det_tangent_redo.
 template <int NM>
-__global__ void __launch_bounds__(128) k_det_tangent(DetArgs a) {
+constexpr int det_tangent_min_blocks() { return NM <= 16 ? 4 : 1; }  // 4 x 39 KB of shared memory at NM = 16
+
+template <int NM>
+__global__ void __launch_bounds__(128, det_tangent_min_blocks<NM>()) k_det_tangent(DetArgs a) {
   extern __shared__ __align__(16) char raw[];
   const long mat = blockIdx.x;
   const MatId m = mat_id(mat, a);
@@ -507,24 +513,26 @@ __global__ void __launch_bounds__(128) k_det_tangent(DetArgs a) {
       a.logdet[mat] = 0.f;
       a.sign[mat] = 1.f;
       a.dlap[mat] = 0.f;
-      a.redo[mat] = 0;
     }
     for (int c = tid; c < n3; c += 128) a.dgrad[mat * n3 + c] = 0.f;
     return;
   }
   const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
   const bool flag = det_tangent_body<NM, float>(a, mat, m, R, raw, true);
-  if (tid == 0) a.redo[mat] = (flag || a.force64) ? 1 : 0;
+  if (tid == 0 && (flag || a.force64)) a.redo[1 + atomicAdd(a.redo, 1)] = (int)mat;
 }
 
+// FP64 redo of the listed matrices (a.redo[0] of them): a small persistent grid.
 template <int NM>
 __global__ void __launch_bounds__(128) k_det_tangent_redo(DetArgs a) {
   extern __shared__ __align__(16) char raw[];
-  const long mat = blockIdx.x;
-  if (!a.redo[mat]) return;  // block-uniform
-  const MatId m = mat_id(mat, a);
-  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
-  det_tangent_body<NM, double>(a, mat, m, R, raw, false);
+  const int count = a.redo[0];
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {  // block-uniform
+    const long mat = a.redo[1 + q];
+    const MatId m = mat_id(mat, a);
+    const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
+    det_tangent_body<NM, double>(a, mat, m, R, raw, false);
+  }
 }
 
 template <int NM>
@@ -540,8 +548,10 @@ void launch_nm(cudaStream_t s, const DetArgs& a) {
       cudaFuncSetAttribute(k_det_tangent_redo<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
       attr = true;
     }
+    cudaMemsetAsync(a.redo, 0, sizeof(int), s);  // empty redo list
     FN_COUNT(1), k_det_tangent<NM><<<(unsigned)nmat, 128, smem, s>>>(a);
-    FN_COUNT(1), k_det_tangent_redo<NM><<<(unsigned)nmat, 128, smem64, s>>>(a);
+    const long redo_blocks = std::min<long>(nmat, 152L * 2);
+    FN_COUNT(1), k_det_tangent_redo<NM><<<(unsigned)redo_blocks, 128, smem64, s>>>(a);
   } else if (NM <= 16 && (long)a.n * a.N * 4 * sizeof(float) <= 32768) {
     const long npair = a.Bc * a.K;
     FN_COUNT(1), k_det_value_pair<NM <= 16 ? NM : 16><<<(unsigned)((npair + 3) / 4), 128,
