@@ -532,93 +532,104 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
           }
         }
       } else {
+        // mode 1, layer of the local-energy pass: tanh with the forward-Laplacian
+        // rule over whole (walker, electron) groups of C columns, one feature per
+        // thread.  Per 8-column chunk: value column (c = 0), derivative columns
+        // (1 <= c <= n3), Laplacian column (n3 + 1), zero padding; only the
+        // first and last chunks mix kinds.
         const int C = a.C, n3 = a.n3;
         const int groups = tile_n / C;
         const float bf = (fok && bias) ? bias[f] : 0.f;
-        const int ldu = (int)a.ldu, ldb = (int)a.ldhb;
+        const long ldb = a.ldhb;
+        // residual in the shared region: 128-byte rows of 64 features whose
+        // 16-byte chunks are permuted by row & 7; chunks start at rows that are
+        // multiples of 8 (C % 8 == 0), so the permutation is fixed per j
+        const int fl = lane_base + lane;
+        const int kbl = fl >> 6, fk = fl & 63;
+        const bool sres = nres > 0 && kbl < nres;
+        const uint8_t* rsh = resr + kbl * (tile_n * BK * 2) + ((fk & 7) << 1);
+        const int chunk = fk >> 3;
+        uint32_t swz[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) swz[j] = (uint32_t)(j * 128 + ((chunk ^ j) << 4));
+        const bool slo = a.res_lo != nullptr;
+        const bool gres = rh && !a.res_smem;
         for (int gi = half; gi < groups; gi += 2) {
           const long r0 = r_tile + (long)gi * C;
           if (r0 >= a.rows) continue;  // warp-uniform: no TMEM access for groups past the end
-          const bool gok = fok;       // per lane: loads and stores only
-          // per-group base pointers; column offsets below fit in 32 bits
-          const float* __restrict__ ug = Up ? Up + ((r0 / a.u_div) * C) * (long)ldu + (fok ? f : 0) : nullptr;
-          const long rb = r0 * (long)ldb + (fok ? f : 0);
-          // pass 1: value column and sum of squared tangents (TMEM only when U
-          // was accumulated by the MMA)
+          const uint32_t tg = tbase + (uint32_t)(gi * C);
+          // pass 1: value column and sum of squared derivative columns
           float z0 = 0.f, sq = 0.f;
           for (int c0 = 0; c0 < C; c0 += 8) {
-            float u8[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) u8[j] = (gok && ug) ? ug[(c0 + j) * ldu] : 0.f;
             float v[8];
-            tmem_ld8(tbase + gi * C + c0, v);
+            tmem_ld8(tg + c0, v);
+            if (c0 >= 1 && c0 + 7 <= n3) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int c = c0 + j;
-              const float z = v[j] + u8[j];
-              z0 = (c == 0) ? z + bf : z0;
-              sq = (c >= 1 && c <= n3) ? fmaf(z, z, sq) : sq;
+              for (int j = 0; j < 8; ++j) sq = fmaf(v[j], v[j], sq);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j;
+                if (c == 0) z0 = v[j] + bf;
+                else if (c <= n3) sq = fmaf(v[j], v[j], sq);
+              }
             }
           }
           const float y = tanhf(z0);
           const float s = 1.f - y * y;
           const float lapc = -2.f * y * s * sq;
-          const __nv_bfloat16* __restrict__ rhg = (rh && !a.res_smem) ? rh + rb : nullptr;
-          const __nv_bfloat16* __restrict__ rlg = (rl && !a.res_smem) ? rl + rb : nullptr;
-          // residual in the shared region: 128-byte swizzled rows of 64 features
-          const int fl = lane_base + lane;
-          const int kbl = fl >> 6, fk = fl & 63;
-          const bool sres = nres > 0 && kbl < nres;
-          const uint8_t* rsh = resr + kbl * (a.tile_n * BK * 2) + ((fk & 7) << 1);
-          const int chunk = fk >> 3;
-          const bool slo = a.res_lo != nullptr;
-          __nv_bfloat16* __restrict__ ohg = oh + rb;
-          __nv_bfloat16* __restrict__ olg = ol ? ol + rb : nullptr;
-          // pass 2: outputs (+ residual), stored as BF16 hi + lo; the global
-          // loads of the next 8-column chunk are issued before the current
-          // chunk is processed
-          auto load8 = [&](float (&r8)[8], int c0) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int off = (c0 + j) * ldb;
-              float v = 0.f;
-              if (gok && rhg) v += __bfloat162float(rhg[off]);
-              if (gok && rlg) v += __bfloat162float(rlg[off]);
-              if (gok && sres) {
-                const int rl_ = gi * C + c0 + j;  // row within the tile
-                const int so = rl_ * 128 + ((chunk ^ (rl_ & 7)) << 4);
-                v += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(rsh + so));
-                if (slo) v += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(rsh + res_half + so));
-              }
-              r8[j] = v;
-            }
-          };
-          auto emit8 = [&](const float (&r8)[8], int c0) {
+          // pass 2: outputs (+ residual) as BF16 hi + lo, pointers advanced per chunk
+          const long rb = r0 * ldb + (fok ? f : 0);
+          __nv_bfloat16* ph = oh + rb;
+          __nv_bfloat16* pl = ol ? ol + rb : nullptr;
+          const __nv_bfloat16* gh = gres ? rh + rb : nullptr;
+          const __nv_bfloat16* gl = (gres && rl) ? rl + rb : nullptr;
+          const uint8_t* rs = rsh + (size_t)(gi * C) * 128;
+          for (int c0 = 0; c0 < C; c0 += 8) {
             float v[8];
-            tmem_ld8(tbase + gi * C + c0, v);
-            if (!gok) return;
+            tmem_ld8(tg + c0, v);
+            if (fok) {
+              float r8[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int c = c0 + j;
-              const float coef = (c >= 1 && c <= n3 + 1) ? s : 0.f;
-              const float z = v[j] + (ug ? ug[c * ldu] : 0.f);
-              float o = (c == 0) ? y : fmaf(coef, z, (c == n3 + 1) ? lapc : 0.f);
-              o += r8[j];  // residual
-              const __nv_bfloat16 h = __float2bfloat16_rn(o);
-              const int off = c * ldb;
-              ohg[off] = h;
-              if (olg) olg[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+              for (int j = 0; j < 8; ++j) {
+                float rv = 0.f;
+                if (sres) {
+                  rv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(rs + swz[j]));
+                  if (slo) rv += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(rs + res_half + swz[j]));
+                } else if (gh) {
+                  rv = __bfloat162float(gh[j * ldb]);
+                  if (gl) rv += __bfloat162float(gl[j * ldb]);
+                }
+                r8[j] = rv;
+              }
+              float o8[8];
+              if (c0 >= 1 && c0 + 7 <= n3) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) o8[j] = fmaf(s, v[j], r8[j]);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const int c = c0 + j;
+                  float o;
+                  if (c == 0) o = y + r8[j];
+                  else if (c <= n3) o = fmaf(s, v[j], r8[j]);
+                  else if (c == n3 + 1) o = fmaf(s, v[j], lapc) + r8[j];
+                  else o = r8[j];
+                  o8[j] = o;
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(o8[j]);
+                ph[j * ldb] = h;
+                if (pl) pl[j * ldb] = __float2bfloat16_rn(o8[j] - __bfloat162float(h));
+              }
             }
-          };
-          float ra[8], rbuf[8];
-          load8(ra, 0);
-          for (int c0 = 0; c0 < C; c0 += 16) {
-            const bool second = c0 + 8 < C;
-            if (second) load8(rbuf, c0 + 8);
-            emit8(ra, c0);
-            if (!second) break;
-            if (c0 + 16 < C) load8(ra, c0 + 16);
-            emit8(rbuf, c0 + 8);
+            ph += 8 * ldb;
+            if (pl) pl += 8 * ldb;
+            if (gh) gh += 8 * ldb;
+            if (gl) gl += 8 * ldb;
+            rs += 8 * 128;
           }
         }
       }
@@ -700,6 +711,7 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
   if (a.stages > STAGES) a.stages = STAGES;
   if (a.stages < 2) return FN_EINVAL;
   if (a.res_smem && (a.mode != 1 || a.tile_n % 8)) return FN_EINVAL;
+  if (a.mode == 1 && (a.U || a.C < 8 || a.C % 8 || a.tile_n % a.C)) return FN_EINVAL;  // layer: no per-walker term
   if (a.tile_n < 16 || a.tile_n > 256 || a.tile_n % 16 || a.nseg < 1 || a.nseg > 3 || a.mode < 0 || a.mode > 2)
     return FN_EINVAL;
   if (a.rm && (a.mode == 1 || (a.mode == 2 && (a.mfeat % 8 || a.ldu % 4 || a.ldhb % 8)) ||

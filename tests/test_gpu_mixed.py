@@ -111,7 +111,10 @@ def test_autotune_and_tuning_roundtrip():
     best = fn.autotune(xx, repeats=1)
     assert fn.get_tuning() == best
     e = fn.local_energy(xx)["eloc"]
-    assert torch.allclose(e, ref, rtol=1e-6, atol=1e-5)
+    # same accumulation order unless the winner takes the residual from shared
+    # memory (see the last check below)
+    tol = 1e-3 if best["residual_smem"] else 1e-6
+    assert torch.allclose(e, ref, rtol=tol, atol=max(tol, 1e-5))
     # other tile shapes keep the accumulation order: same results
     fn.set_tuning(layer_groups=4, feature_tile=128, tangent_chunk=17, residual_smem=0)
     e2 = fn.local_energy(xx)["eloc"]
