@@ -12,6 +12,8 @@
 // derivatives (product rule; the envelope depends on r_j only).
 #include <math.h>
 
+#include <type_traits>
+
 #include "fn_internal.cuh"
 
 namespace fn {
@@ -87,6 +89,70 @@ __device__ __forceinline__ void warp_gj(T (&a)[NM], T (&b)[NM], int n, int lane,
       }
     }
   }
+}
+
+// log|det| and sign of the n x n matrices held by the two 16-lane halves of a
+// warp (row sl in lane sl of each half; rows n..15 unused), by LU with partial
+// pivoting in FP32, without inverse rows.  Rows are never moved: the pivot of
+// step k is the unused row with the largest |a_k| (one warp-wide max over
+// 32-bit keys whose low 4 bits hold 15 - row, so ties go to the lower row), and
+// the sign of the row permutation is counted from the rows already pivoted.
+// The product of pivots is kept as mantissa and exponent (one log at the end).
+// All lanes of a half end with the same results; padding rows (index >= nreal)
+// do not enter the pivot extremes.  A pivot below the smallest normal float
+// leaves the matrix to the FP64 redo (the pivot ratio flags it).
+template <int NM>
+__device__ __forceinline__ void warp_lu16(float (&a)[NM], int n, int sl, float& logabs, float& sgn, float& pmin,
+                                          float& pmax, bool& sing, int nreal) {
+  const int half = (threadIdx.x >> 4) & 1;
+  const unsigned hbits = half ? 0xFFFF0000u : 0x0000FFFFu;
+  bool pivoted = false;
+  float mant = 1.f, s = 1.f;
+  int expo = 0;
+  pmin = INFINITY;
+  pmax = 0.f;
+  sing = false;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    if (k >= n) break;
+    const unsigned cand = (!pivoted && sl < n)
+                              ? ((__float_as_uint(fabsf(a[k])) & ~0xFu) | (unsigned)(15 - sl))
+                              : 0u;
+    const unsigned m0 = __reduce_max_sync(FULL, half ? 0u : cand);
+    const unsigned m1 = __reduce_max_sync(FULL, half ? cand : 0u);
+    const int p = 15 - (int)((half ? m1 : m0) & 0xFu);
+    // rows pivoted before p with a larger index: inversions of the permutation
+    const unsigned done = __ballot_sync(FULL, pivoted) & hbits;
+    const unsigned above = (half ? (0xFFFF0000u << (p + 1)) : ((0xFFFFu << (p + 1)) & 0xFFFFu)) & done;
+    if (__popc(above) & 1) s = -s;
+    const float u = __shfl_sync(FULL, a[k], p, 16);
+    const float au = fabsf(u);
+    if (k < nreal) {
+      pmin = fminf(pmin, au);
+      pmax = fmaxf(pmax, au);
+    }
+    if (!(au > 0.f)) sing = true;
+    if (u < 0.f) s = -s;
+    // running product of |pivots| as mant * 2^expo
+    mant *= sing ? 1.f : au;
+    const unsigned mb = __float_as_uint(mant);
+    expo += (int)((mb >> 23) & 0xFFu) - 127;
+    mant = __uint_as_float((mb & 0x807FFFFFu) | 0x3F800000u);
+    if (sl == p) pivoted = true;
+    // the update of Gauss-Jordan: the pivot row is scaled first, so a column
+    // equal to an earlier one eliminates to an exact zero
+    const float iu = sing ? 0.f : 1.f / u;
+    const float fct = pivoted ? 0.f : a[k];
+#pragma unroll
+    for (int c = 0; c < NM; ++c) {
+      if (c > k) {
+        const float rk = __shfl_sync(FULL, a[c], p, 16) * iu;
+        a[c] = fmaf(-fct, rk, a[c]);
+      }
+    }
+  }
+  logabs = logf(mant) + (float)expo * 0.69314718055994531f;
+  sgn = s;
 }
 
 struct MatId {
@@ -168,10 +234,10 @@ __device__ bool det_value_body(const DetArgs& a, long mat, const MatId& m, int l
   if (lane == 0) {
     a.logdet[mat] = sing ? -INFINITY : (float)logabs;
     a.sign[mat] = sing ? 0.f : (float)sgn;
-    if (count) {
-      if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
-      else if (flag) atomicAdd(a.flagged, 1ull);
-    }
+    // a singular result is reported by whichever pass settles the matrix
+    // (the FP64 redo included); the flagged count belongs to the FP32 pass
+    if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
+    else if (flag && count) atomicAdd(a.flagged, 1ull);
   }
   if (a.minv && lane < m.ns) {
 #pragma unroll
@@ -212,12 +278,36 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
                               bool count) {
   T ra[NM], rb[NM];
   const long NSS = a.nss;
+  // determinant only, in FP32: half-warp LU and fast exponentials (the stored
+  // forward of the adjoint keeps the accurate path)
+  bool fast = false;
+  if constexpr (std::is_same<T, float>::value) fast = !a.minv && !a.env;
 #pragma unroll
   for (int c = 0; c < NM; ++c) {
     ra[c] = (c == sl) ? T(1) : T(0);
     rb[c] = (c == sl) ? T(1) : T(0);
   }
-  if (sl < m.ns) {
+  if (fast && sl < m.ns) {
+    // nuclei outer, this lane's columns inner: pi and sigma loaded once per
+    // nucleus, exp(-|sigma| d) as 2^(-|sigma| log2(e) d)
+    const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
+    const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + sl) * a.N;
+    float ev[NM];
+#pragma unroll
+    for (int c = 0; c < NM; ++c) ev[c] = 0.f;
+    for (int mm = 0; mm < a.N; ++mm) {
+      const float pm = pi[mm], sm2 = -fabsf(sg[mm]) * 1.4426950408889634f;
+      const float* dm = dist + m.j0 * a.N + mm;
+#pragma unroll
+      for (int c = 0; c < NM; ++c)
+        if (c < m.ns) ev[c] = fmaf(pm, exp2f(sm2 * dm[c * a.N]), ev[c]);
+    }
+    const float* ob = a.O + (m.w * a.n + m.j0) * (long)a.C * a.ldo + m.q0 + sl;
+    const int ostride = (int)(a.C * a.ldo);
+#pragma unroll
+    for (int c = 0; c < NM; ++c)
+      if (c < m.ns) ra[c] = (T)(ob[c * ostride] * ev[c]);
+  } else if (sl < m.ns) {
     const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
     const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + sl) * a.N;
 #pragma unroll
@@ -235,18 +325,26 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
   }
   T logabs, sgn, pmin, pmax;
   bool sing;
-  if (a.minv)
+  bool done = false;
+  if (a.minv) {
     warp_gj<NM, T, 16, true>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
-  else
-    warp_gj<NM, T, 16, false>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
+    done = true;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (!done && fast) {
+      warp_lu16<NM>(ra, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
+      done = true;
+    }
+  }
+  if (!done) warp_gj<NM, T, 16, false>(ra, rb, nmax, sl, logabs, sgn, pmin, pmax, sing, m.ns);
   const bool flag = !sing && pmin < (T)a.pivot_tau * pmax;
   if (sl == 0) {
     a.logdet[mat] = sing ? -INFINITY : (float)logabs;
     a.sign[mat] = sing ? 0.f : (float)sgn;
-    if (count) {
-      if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
-      else if (flag) atomicAdd(a.flagged, 1ull);
-    }
+    // a singular result is reported by whichever pass settles the matrix
+    // (the FP64 redo included); the flagged count belongs to the FP32 pass
+    if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
+    else if (flag && count) atomicAdd(a.flagged, 1ull);
   }
   if (a.minv && sl < m.ns) {
 #pragma unroll
@@ -411,10 +509,10 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
       a.sign[mat] = sing ? 0.f : (float)sgn;
       sing_s = sing ? 1 : 0;
       flag_s = flag ? 1 : 0;
-      if (count) {
-        if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
-        else if (flag) atomicAdd(a.flagged, 1ull);
-      }
+      // a singular result is reported by whichever pass settles the matrix
+      // (the FP64 redo included); the flagged count belongs to the FP32 pass
+      if (sing) atomicOr(a.status, (unsigned)ST_SINGULAR);
+      else if (flag && count) atomicAdd(a.flagged, 1ull);
     }
   }
   __syncthreads();
