@@ -654,6 +654,10 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
   }
   float* tn_scr = ar.get<float>(tn_max);
   double* cs_scr = ar.get<double>(cs_max);
+  // fused two-electron backward (k_pair.cu) where its kernels cover the widths
+  bool pair_bwd = c->tune.pair_unfused == 0;
+  for (int l = 0; l < L - 1 && pair_bwd; ++l) pair_bwd = pair_bwd_supported(din2_of(t, l), d2);
+  float* pb_scr = pair_bwd ? ar.get<float>(pair_bwd_scratch_floats(d2, d2)) : nullptr;
   if (ar.measure) return;
 
   cudaStream_t s = c->stream;
@@ -696,7 +700,22 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
     const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
     const float* V = P + Lo.V[l];
     float* Ecur = Ebar[eb];
-    if (l < L - 1) {
+    if (l < L - 1 && pair_bwd) {
+      // one pass: tanh backward, dW, dc and (l >= 1) the input gradient with
+      // the residual; layer 0's input gradient is not needed
+      PairBwdArgs pb{};
+      pb.Eout_bar = Enext;
+      pb.Y = st.Y2[l];
+      pb.Ein = st.E[l];
+      pb.W = P + Lo.W[l];
+      pb.Ein_bar = l >= 1 ? Ecur : nullptr;
+      pb.residual = l >= 1 ? 1 : 0;
+      pb.pairs = pairs;
+      pb.grad_W = grad + Lo.W[l];
+      pb.grad_c = grad + Lo.c[l];
+      pb.partial = pb_scr;
+      if (!launch_pair_bwd(s, pb, a2, d2)) c->host_fail = true;
+    } else if (l < L - 1) {
       launch_tanh_bwd(s, Enext, st.Y2[l], pairs, d2, Z2bar);
       TN(d2, a2, pairs, Z2bar, d2, st.E[l], a2, grad + Lo.W[l], a2);
       launch_colsum_accum(s, Z2bar, pairs, d2, d2, grad + Lo.c[l], cs_scr);

@@ -117,6 +117,26 @@ struct PairArgs {
 bool pair_layer_supported(int n, int din, int dout, bool layer, int Q, int C, long ldm);
 bool launch_pair_layer(cudaStream_t s, const PairArgs& a, int din, int dout, int Q);
 
+// Backward of a two-electron layer of the value pass (k_pair.cu): with
+// Zbar = Eout_bar * (1 - y^2), accumulates dW = Zbar^T Ein and dc = sum Zbar
+// into grad (FP64, by way of per-block FP32 partials summed in block order) and
+// writes Ein_bar = Zbar W (+ Eout_bar when residual) unless Ein_bar is null.
+struct PairBwdArgs {
+  const float* Eout_bar;  // [pairs][dout]
+  const float* Y;         // [pairs][dout] tanh values
+  const float* Ein;       // [pairs][din]
+  const float* W;         // [dout][din]
+  float* Ein_bar;         // [pairs][din] or null
+  int residual;
+  long pairs;
+  double* grad_W;         // [dout][din]
+  double* grad_c;         // [dout]
+  float* partial;         // scratch: pair_bwd_scratch_floats(din, dout) floats
+};
+bool pair_bwd_supported(int din, int dout);
+long pair_bwd_scratch_floats(int din, int dout);
+bool launch_pair_bwd(cudaStream_t s, const PairBwdArgs& a, int din, int dout);
+
 // ---------------------------------------------------------------------------
 // Determinants (k_det.cu)
 struct DetArgs {

@@ -330,7 +330,152 @@ bool dispatch(cudaStream_t s, const PairArgs& a, int din, int dout) {
   return false;
 }
 
+// ---------------------------------------------------------------------------
+// Backward of the two-electron layer (value pass, for the parameter adjoint)
+
+constexpr int kBwdPairs = 96;  // pairs per tile (static shared memory under 48 KB)
+constexpr int kBwdMaxBlocks = 152 * 4;
+
+// One tile of kBwdPairs pairs per step of a persistent grid.  Shared tiles:
+// Zbar and Eout_bar [P][DO + 1], Ein [P][DIN + 1], W [DO][DIN].  Thread t owns
+// dW[f][k0 .. k0 + 3] (f = t / (DIN / 4)) and, for k0 == 0, dc[f]; the
+// input-gradient rows are 4 features per task.
+template <int DIN, int DO>
+__global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
+  constexpr int P = kBwdPairs, ZS = DO + 1, ES = DIN + 1;
+  __shared__ float Zt[P * ZS];
+  __shared__ float Ot[P * ZS];
+  __shared__ float Et[P * ES];
+  __shared__ float Ws[DO * DIN];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < DO * DIN; t += 256) Ws[t] = a.W[t];
+  constexpr int NW = DO * DIN / 4;  // dW owners
+  const bool own = tid < NW;
+  const int f = own ? tid / (DIN / 4) : 0, k0 = own ? (tid % (DIN / 4)) * 4 : 0;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f}, cacc = 0.f;
+  const long n_tiles = (a.pairs + P - 1) / P;
+  for (long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long p0 = tile * P;
+    const int np = (int)min((long)P, a.pairs - p0);
+    __syncthreads();  // previous tile fully used
+    for (int t = tid; t < np * (DO / 4); t += 256) {
+      const int p = t / (DO / 4), q = (t % (DO / 4)) * 4;
+      const float4 ob = *reinterpret_cast<const float4*>(a.Eout_bar + (p0 + p) * DO + q);
+      const float4 y = *reinterpret_cast<const float4*>(a.Y + (p0 + p) * DO + q);
+      float* zr = Zt + p * ZS + q;
+      float* orr = Ot + p * ZS + q;
+      zr[0] = ob.x * (1.f - y.x * y.x);
+      zr[1] = ob.y * (1.f - y.y * y.y);
+      zr[2] = ob.z * (1.f - y.z * y.z);
+      zr[3] = ob.w * (1.f - y.w * y.w);
+      orr[0] = ob.x;
+      orr[1] = ob.y;
+      orr[2] = ob.z;
+      orr[3] = ob.w;
+    }
+    for (int t = tid; t < np * (DIN / 4); t += 256) {
+      const int p = t / (DIN / 4), q = (t % (DIN / 4)) * 4;
+      const float4 e = *reinterpret_cast<const float4*>(a.Ein + (p0 + p) * DIN + q);
+      float* er = Et + p * ES + q;
+      er[0] = e.x;
+      er[1] = e.y;
+      er[2] = e.z;
+      er[3] = e.w;
+    }
+    __syncthreads();
+    if (own) {
+      for (int p = 0; p < np; ++p) {
+        const float z = Zt[p * ZS + f];
+        const float* e = Et + p * ES + k0;
+        acc[0] = fmaf(z, e[0], acc[0]);
+        acc[1] = fmaf(z, e[1], acc[1]);
+        acc[2] = fmaf(z, e[2], acc[2]);
+        acc[3] = fmaf(z, e[3], acc[3]);
+        cacc += z;
+      }
+    }
+    if (a.Ein_bar) {
+      for (int t = tid; t < np * (DIN / 4); t += 256) {
+        const int p = t / (DIN / 4), q = (t % (DIN / 4)) * 4;
+        const float* z = Zt + p * ZS;
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int ff = 0; ff < DO; ++ff) {
+          const float zf = z[ff];
+          const float* w = Ws + ff * DIN + q;
+          o[0] = fmaf(zf, w[0], o[0]);
+          o[1] = fmaf(zf, w[1], o[1]);
+          o[2] = fmaf(zf, w[2], o[2]);
+          o[3] = fmaf(zf, w[3], o[3]);
+        }
+        if (a.residual) {
+          const float* r = Ot + p * ZS + q;
+          o[0] += r[0];
+          o[1] += r[1];
+          o[2] += r[2];
+          o[3] += r[3];
+        }
+        *reinterpret_cast<float4*>(a.Ein_bar + (p0 + p) * DIN + q) = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    }
+  }
+  // this block's partial sums
+  constexpr int PS = DO * DIN + DO;
+  float* part = a.partial + (long)blockIdx.x * PS;
+  if (own) {
+    part[f * DIN + k0] = acc[0];
+    part[f * DIN + k0 + 1] = acc[1];
+    part[f * DIN + k0 + 2] = acc[2];
+    part[f * DIN + k0 + 3] = acc[3];
+    if (k0 == 0) part[DO * DIN + f] = cacc;
+  }
+}
+
+// grad[j] += sum over blocks of the partials, in FP64 and block order.
+__global__ void k_pair_bwd_reduce(const float* __restrict__ part, int nblocks, int ps, int nw, double* grad_W,
+                                  double* grad_c) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ps) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += (double)part[(long)b * ps + j];
+  if (j < nw) grad_W[j] += s;
+  else grad_c[j - nw] += s;
+}
+
+template <int DIN, int DO>
+void launch_bwd_inst(cudaStream_t s, const PairBwdArgs& a) {
+  int occ = 0, dev = 0, sms = 152;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_bwd<DIN, DO>, 256, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long tiles = (a.pairs + kBwdPairs - 1) / kBwdPairs;
+  long blocks = std::min<long>(tiles, (long)sms * occ);
+  if (blocks > kBwdMaxBlocks) blocks = kBwdMaxBlocks;
+  FN_COUNT(1), k_pair_bwd<DIN, DO><<<(unsigned)blocks, 256, 0, s>>>(a);
+  const int ps = DO * DIN + DO;
+  FN_COUNT(1), k_pair_bwd_reduce<<<(ps + 255) / 256, 256, 0, s>>>(a.partial, (int)blocks, ps, DO * DIN, a.grad_W,
+                                                                   a.grad_c);
+}
+
 }  // namespace
+
+bool pair_bwd_supported(int din, int dout) {
+  return (dout == 8 || dout == 16 || dout == 32) && (din == 4 || din == dout);
+}
+
+long pair_bwd_scratch_floats(int din, int dout) { return (long)kBwdMaxBlocks * (dout * din + dout); }
+
+bool launch_pair_bwd(cudaStream_t s, const PairBwdArgs& a, int din, int dout) {
+  if (a.pairs <= 0) return true;
+  if (din == 4 && dout == 8) return launch_bwd_inst<4, 8>(s, a), true;
+  if (din == 8 && dout == 8) return launch_bwd_inst<8, 8>(s, a), true;
+  if (din == 4 && dout == 16) return launch_bwd_inst<4, 16>(s, a), true;
+  if (din == 16 && dout == 16) return launch_bwd_inst<16, 16>(s, a), true;
+  if (din == 4 && dout == 32) return launch_bwd_inst<4, 32>(s, a), true;
+  if (din == 32 && dout == 32) return launch_bwd_inst<32, 32>(s, a), true;
+  return false;
+}
 
 bool pair_layer_supported(int n, int din, int dout, bool layer, int Q, int C, long ldm) {
   const bool din_ok = din == 4 || din == 8 || din == 16 || din == 32;
