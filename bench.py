@@ -185,13 +185,20 @@ def run_reference(args, wl):
 # ---------------------------------------------------------------------------
 
 def kernel_source_hash() -> str:
-    """Hash of the sources of the timed GEMM class (tensor-core and SIMT GEMMs
-    and the schedule that sizes their launches)."""
+    """Hash of what the timed GEMM class's traffic depends on: the tensor-core
+    GEMM sources and the network pass (forward() in ferminet.cu) that sizes
+    and tiles its launches."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("k_tc_gemm.cu", "tc_gemm.cuh", "k_gemm.cu", "ferminet.cu"):
-        with open(os.path.join(ROOT, "paper_2011_07125_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_2011_07125_gb300", "csrc")
+    for f in ("k_tc_gemm.cu", "tc_gemm.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "ferminet.cu"), "rb") as fh:
+        src = fh.read()
+    start = src.find(b"\nvoid forward(fn_ctx* c")
+    end = src.find(b"\n}\n", start)
+    h.update(src[start:end] if start >= 0 and end > start else src)
     return h.hexdigest()[:16]
 
 
