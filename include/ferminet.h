@@ -155,7 +155,8 @@ fn_status ferminet_logpsi_vjp(fn_ctx* ctx, const float* d_x, long B, const float
 /* VMC energy gradient (Eq. 2 differentiated with E_L held fixed).  For every
  * geometry g, d_emean[g] (double, [n_geoms]) = mean of d_eloc over its walkers,
  * and d_grad [n_params] = sum_g 2/B_g sum_{w in g} (E_L,w - E_mean,g)
- * d log|psi_w| / d theta, reduced in FP64 and stored as float. */
+ * d log|psi_w| / d theta, stored as float.  The sum over walkers runs in FP32
+ * over blocks of at most a few thousand rows and in FP64 across blocks. */
 fn_status ferminet_energy_grad(fn_ctx* ctx, const float* d_x, long B, const float* d_eloc, double* d_emean,
                                float* d_grad);
 

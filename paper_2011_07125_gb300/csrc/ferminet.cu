@@ -696,6 +696,7 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
   gemm_nn(s, rows, d1, Ktot, Obar, Ktot, P + Lo.w_orb, d1, Hbar[0], d1, Epi{});
   int hb = 0, eb = 0;
   float* Enext = nullptr;
+  bool spread_pending = false;  // fused path: M2bar holds layer l + 1's pair-mean gradient
   for (int l = L - 1; l >= 0; --l) {
     const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
     const float* V = P + Lo.V[l];
@@ -705,6 +706,9 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
       // the residual; layer 0's input gradient is not needed
       PairBwdArgs pb{};
       pb.Eout_bar = Enext;
+      pb.M2bar = spread_pending ? M2bar : nullptr;
+      pb.n = n;
+      pb.n_up = t.n_up;
       pb.Y = st.Y2[l];
       pb.Ein = st.E[l];
       pb.W = P + Lo.W[l];
@@ -721,7 +725,7 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
       launch_colsum_accum(s, Z2bar, pairs, d2, d2, grad + Lo.c[l], cs_scr);
       gemm_nn(s, pairs, a2, d2, Z2bar, d2, P + Lo.W[l], a2, Ecur, a2, Epi{});
       if (l >= 1) launch_add(s, Ecur, Enext, pairs * a2);
-    } else {
+    } else if (!pair_bwd) {
       cudaMemsetAsync(Ecur, 0, sizeof(float) * pairs * a2, s);
     }
     float* Hcur = Hbar[hb];
@@ -738,10 +742,11 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
       gemm_nn(s, Bc, 2 * a1, d1, S, d1, V + a1, wV, M1bar, 2 * a1, Epi{});
       launch_spread_mean1(s, M1bar, Bc, n, t.n_up, a1, Hprev);
       gemm_nn(s, rows, 2 * a2, d1, Zbar, d1, V + 3 * a1, wV, M2bar, 2 * a2, Epi{});
-      launch_spread_mean2(s, M2bar, Bc, n, t.n_up, a2, Ecur);
+      if (pair_bwd) spread_pending = true;  // added by the next pair backward as it loads
+      else launch_spread_mean2(s, M2bar, Bc, n, t.n_up, a2, Ecur);
       hb ^= 1;
     }
-    Enext = Ecur;
+    Enext = (pair_bwd && l == L - 1) ? nullptr : Ecur;
     eb ^= 1;
   }
 }

@@ -122,7 +122,9 @@ bool launch_pair_layer(cudaStream_t s, const PairArgs& a, int din, int dout, int
 // into grad (FP64, by way of per-block FP32 partials summed in block order) and
 // writes Ein_bar = Zbar W (+ Eout_bar when residual) unless Ein_bar is null.
 struct PairBwdArgs {
-  const float* Eout_bar;  // [pairs][dout]
+  const float* Eout_bar;  // [pairs][dout], or null (zero)
+  const float* M2bar;     // gradient of the next layer's pair means [groups][2 dout], or null: its
+  int n, n_up;            // share M2bar[w i][spin(j)] / n_spin(j) is added to Eout_bar of pair (i, j)
   const float* Y;         // [pairs][dout] tanh values
   const float* Ein;       // [pairs][din]
   const float* W;         // [dout][din]

@@ -70,10 +70,11 @@ __global__ void k_colsum_part(const float* __restrict__ X, long rows, long cols,
   const long c = (long)blockIdx.x * 32 + tx;
   const long r0 = (long)blockIdx.y * rpc;
   const long r1 = min(rows, r0 + rpc);
-  double s = 0.0;
+  // FP32 over this thread's rows (a few hundred), FP64 from here on
+  float s = 0.f;
   if (c < cols)
-    for (long r = r0 + ty; r < r1; r += 8) s += (double)X[r * ldx + c];
-  sh[ty][tx] = s;
+    for (long r = r0 + ty; r < r1; r += 8) s += X[r * ldx + c];
+  sh[ty][tx] = (double)s;
   __syncthreads();
   if (ty == 0 && c < cols) {
     double t = 0.0;

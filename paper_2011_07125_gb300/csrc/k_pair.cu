@@ -360,7 +360,18 @@ __global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
     __syncthreads();  // previous tile fully used
     for (int t = tid; t < np * (DO / 4); t += 256) {
       const int p = t / (DO / 4), q = (t % (DO / 4)) * 4;
-      const float4 ob = *reinterpret_cast<const float4*>(a.Eout_bar + (p0 + p) * DO + q);
+      float4 ob = a.Eout_bar ? *reinterpret_cast<const float4*>(a.Eout_bar + (p0 + p) * DO + q)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.M2bar) {  // the next layer's pair-mean gradient, spread over the pairs it averaged
+        const long gp = p0 + p, wi = gp / a.n;
+        const int j = (int)(gp - wi * a.n), sj = j < a.n_up ? 0 : 1;
+        const float ns = (float)(sj == 0 ? a.n_up : a.n - a.n_up);
+        const float4 m = *reinterpret_cast<const float4*>(a.M2bar + wi * 2 * DO + sj * DO + q);
+        ob.x += m.x / ns;
+        ob.y += m.y / ns;
+        ob.z += m.z / ns;
+        ob.w += m.w / ns;
+      }
       const float4 y = *reinterpret_cast<const float4*>(a.Y + (p0 + p) * DO + q);
       float* zr = Zt + p * ZS + q;
       float* orr = Ot + p * ZS + q;
