@@ -760,9 +760,24 @@ size_t ws_bytes(fn_ctx* c, long Bc, int mode) {
   return ar.off;
 }
 
-// Largest chunk whose workspace fits the budget (FERMINET_WS_GB, default 24).
+// Workspace budget: 30% of the device's memory, at most 80 GB (GB300: the
+// whole 4096-walker local-energy pass in one chunk); FERMINET_WS_GB overrides.
+double default_ws_gb() {
+  static double gb = -1.0;
+  if (gb < 0.0) {
+    size_t freeb = 0, total = 0;
+    gb = 24.0;
+    if (cudaMemGetInfo(&freeb, &total) == cudaSuccess && total > 0)
+      gb = std::min(80.0, 0.3 * (double)total / (double)(1ull << 30));
+    else
+      cudaGetLastError();
+  }
+  return gb;
+}
+
+// Largest chunk whose workspace fits the budget.
 long chunk_for(fn_ctx* c, long B, int mode) {
-  double gb = 24.0;
+  double gb = default_ws_gb();
   if (const char* v = getenv("FERMINET_WS_GB")) gb = atof(v);
   const double budget = gb * (1ull << 30);
   const double b1 = (double)ws_bytes(c, 1, mode), b2 = (double)ws_bytes(c, 2, mode);
