@@ -342,11 +342,13 @@ constexpr int kBwdMaxBlocks = 152 * 4;
 // input-gradient rows are 4 features per task.
 template <int DIN, int DO>
 __global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
-  constexpr int P = kBwdPairs, ZS = DO + 1, ES = DIN + 1;
+  // Ein rows padded to a multiple of 4 floats: the dW loop reads 4 features of
+  // one row per thread (all threads on the same row: no bank conflict)
+  constexpr int P = kBwdPairs, ZS = DO + 1, ES = DIN + 4;
   __shared__ float Zt[P * ZS];
   __shared__ float Ot[P * ZS];
-  __shared__ float Et[P * ES];
-  __shared__ float Ws[DO * DIN];
+  __shared__ __align__(16) float Et[P * ES];
+  __shared__ __align__(16) float Ws[DO * DIN];
   const int tid = threadIdx.x;
   for (int t = tid; t < DO * DIN; t += 256) Ws[t] = a.W[t];
   constexpr int NW = DO * DIN / 4;  // dW owners
@@ -386,22 +388,17 @@ __global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
     }
     for (int t = tid; t < np * (DIN / 4); t += 256) {
       const int p = t / (DIN / 4), q = (t % (DIN / 4)) * 4;
-      const float4 e = *reinterpret_cast<const float4*>(a.Ein + (p0 + p) * DIN + q);
-      float* er = Et + p * ES + q;
-      er[0] = e.x;
-      er[1] = e.y;
-      er[2] = e.z;
-      er[3] = e.w;
+      *reinterpret_cast<float4*>(Et + p * ES + q) = *reinterpret_cast<const float4*>(a.Ein + (p0 + p) * DIN + q);
     }
     __syncthreads();
     if (own) {
       for (int p = 0; p < np; ++p) {
         const float z = Zt[p * ZS + f];
-        const float* e = Et + p * ES + k0;
-        acc[0] = fmaf(z, e[0], acc[0]);
-        acc[1] = fmaf(z, e[1], acc[1]);
-        acc[2] = fmaf(z, e[2], acc[2]);
-        acc[3] = fmaf(z, e[3], acc[3]);
+        const float4 e = *reinterpret_cast<const float4*>(Et + p * ES + k0);
+        acc[0] = fmaf(z, e.x, acc[0]);
+        acc[1] = fmaf(z, e.y, acc[1]);
+        acc[2] = fmaf(z, e.z, acc[2]);
+        acc[3] = fmaf(z, e.w, acc[3]);
         cacc += z;
       }
     }
@@ -413,11 +410,11 @@ __global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
 #pragma unroll 8
         for (int ff = 0; ff < DO; ++ff) {
           const float zf = z[ff];
-          const float* w = Ws + ff * DIN + q;
-          o[0] = fmaf(zf, w[0], o[0]);
-          o[1] = fmaf(zf, w[1], o[1]);
-          o[2] = fmaf(zf, w[2], o[2]);
-          o[3] = fmaf(zf, w[3], o[3]);
+          const float4 w = *reinterpret_cast<const float4*>(Ws + ff * DIN + q);
+          o[0] = fmaf(zf, w.x, o[0]);
+          o[1] = fmaf(zf, w.y, o[1]);
+          o[2] = fmaf(zf, w.z, o[2]);
+          o[3] = fmaf(zf, w.w, o[3]);
         }
         if (a.residual) {
           const float* r = Ot + p * ZS + q;
