@@ -288,7 +288,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   float* sgn = ar.get<float>(Bc * K * 2);
   float* dgrad = tangent ? ar.get<float>(Bc * K * 2 * 3 * n) : nullptr;
   float* dlap = tangent ? ar.get<float>(Bc * K * 2) : nullptr;
-  int* redo = tangent ? ar.get<int>(1 + Bc * K * 2) : nullptr;
+  int* redo = ar.get<int>(1 + Bc * K * 2);  // FP64 redo list of the determinant kernels
   const long nss = (long)c->ns_max * c->ns_max;
   if (store) {
     st->O = O;

@@ -162,7 +162,8 @@ struct DetArgs {
   float pivot_tau;
   long nss;            // stride between stored matrices (ns_max^2)
   int force64;         // redo every matrix in FP64 (diagnostics)
-  int* redo;           // [1 + Bc K 2]: count, then the matrices to redo in FP64 (tangent pass)
+  int* redo;           // [1 + Bc K 2]: count, then the matrices (tangent pass) or determinant
+                       // pairs (value pass) to redo in FP64
 };
 void launch_det(cudaStream_t s, const DetArgs& a);
 

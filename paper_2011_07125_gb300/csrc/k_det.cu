@@ -354,6 +354,24 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
   return flag;
 }
 
+// Distances |r_j - R_m| of walker w for all electrons and nuclei, in the warp's
+// shared slice.
+__device__ __forceinline__ void pair_distances(const DetArgs& a, const MatId& m, int lane, float* dist) {
+  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
+  for (int t = lane; t < a.n * a.N; t += 32) {
+    const int j = t / a.N, mm = t % a.N;
+    const float* xj = a.x + (m.w * a.n + j) * 3;
+    const float d0 = xj[0] - R[3 * mm], d1 = xj[1] - R[3 * mm + 1], d2 = xj[2] - R[3 * mm + 2];
+    dist[t] = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  }
+  __syncwarp();
+}
+
+// Value pass: a warp per determinant k of a walker, its two spin matrices in
+// the 16-lane halves.  A pair with a matrix whose FP32 pivot ratio falls below
+// pivot_tau is appended to the list a.redo and done again in FP64 by
+// k_det_value_pair_redo (kept out of this kernel, whose registers it would
+// otherwise set).
 template <int NM>
 __global__ void __launch_bounds__(128) k_det_value_pair(DetArgs a) {
   extern __shared__ float dsh[];
@@ -365,32 +383,37 @@ __global__ void __launch_bounds__(128) k_det_value_pair(DetArgs a) {
   const long mat = 2 * pair + half;
   const MatId m = mat_id(mat, a);
   float* dist = dsh + warp * a.n * a.N;
-  const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
-  for (int t = lane; t < a.n * a.N; t += 32) {
-    const int j = t / a.N, mm = t % a.N;
-    const float* xj = a.x + (m.w * a.n + j) * 3;
-    const float d0 = xj[0] - R[3 * mm], d1 = xj[1] - R[3 * mm + 1], d2 = xj[2] - R[3 * mm + 2];
-    dist[t] = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-  }
-  __syncwarp();
+  pair_distances(a, m, lane, dist);
   const int nmax = a.n_up > a.n - a.n_up ? a.n_up : a.n - a.n_up;
-  if (m.ns == 0 && sl == 0) {
-    a.logdet[mat] = 0.f;
-    a.sign[mat] = 1.f;
-  }
-  bool flag = false;
   // an empty spin channel (ns = 0) still takes part in the warp-wide shuffles
-  flag = det_pair_body<NM, float>(a, mat, m, sl, nmax, dist, true) && m.ns > 0;
+  const bool flag = det_pair_body<NM, float>(a, mat, m, sl, nmax, dist, true) && m.ns > 0;
   if (m.ns == 0 && sl == 0) {
     a.logdet[mat] = 0.f;
     a.sign[mat] = 1.f;
   }
-  if (__any_sync(FULL, flag || a.force64)) {
+  if (__any_sync(FULL, flag || a.force64) && lane == 0) a.redo[1 + atomicAdd(a.redo, 1)] = (int)pair;
+}
+
+// FP64 redo of the listed pairs (a.redo[0] of them), a warp per pair.
+template <int NM>
+__global__ void __launch_bounds__(128) k_det_value_pair_redo(DetArgs a) {
+  extern __shared__ float dsh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, sl = lane & 15;
+  const int count = a.redo[0];
+  float* dist = dsh + warp * a.n * a.N;
+  const int nmax = a.n_up > a.n - a.n_up ? a.n_up : a.n - a.n_up;
+  for (int q = blockIdx.x * 4 + warp; q < count; q += gridDim.x * 4) {  // warp-uniform
+    const long pair = a.redo[1 + q];
+    const long mat = 2 * pair + half;
+    const MatId m = mat_id(mat, a);
+    pair_distances(a, m, lane, dist);
     det_pair_body<NM, double>(a, mat, m, sl, nmax, dist, false);
     if (m.ns == 0 && sl == 0) {
       a.logdet[mat] = 0.f;
       a.sign[mat] = 1.f;
     }
+    __syncwarp();  // the distance slice is refilled for the next pair
   }
 }
 
@@ -650,10 +673,13 @@ void launch_nm(cudaStream_t s, const DetArgs& a) {
     FN_COUNT(1), k_det_tangent<NM><<<(unsigned)nmat, 128, smem, s>>>(a);
     const long redo_blocks = std::min<long>(nmat, 152L * 2);
     FN_COUNT(1), k_det_tangent_redo<NM><<<(unsigned)redo_blocks, 128, smem64, s>>>(a);
-  } else if (NM <= 16 && (long)a.n * a.N * 4 * sizeof(float) <= 32768) {
+  } else if (NM <= 16 && a.redo && (long)a.n * a.N * 4 * sizeof(float) <= 32768) {
     const long npair = a.Bc * a.K;
-    FN_COUNT(1), k_det_value_pair<NM <= 16 ? NM : 16><<<(unsigned)((npair + 3) / 4), 128,
-                                                         sizeof(float) * 4 * a.n * a.N, s>>>(a);
+    const size_t sm = sizeof(float) * 4 * a.n * a.N;
+    cudaMemsetAsync(a.redo, 0, sizeof(int), s);  // empty redo list
+    FN_COUNT(1), k_det_value_pair<NM <= 16 ? NM : 16><<<(unsigned)((npair + 3) / 4), 128, sm, s>>>(a);
+    const long redo_blocks = std::min<long>((npair + 3) / 4, 152L * 2);
+    FN_COUNT(1), k_det_value_pair_redo<NM <= 16 ? NM : 16><<<(unsigned)redo_blocks, 128, sm, s>>>(a);
   } else {
     FN_COUNT(1), k_det_value<NM><<<(unsigned)((nmat + 3) / 4), 128, 0, s>>>(a);
   }
