@@ -219,7 +219,26 @@ def recorded_traffic(workload: str, prec: str):
     return None
 
 
-def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_launch=None):
+def gemm_class_alg_bytes(net) -> float:
+    """Algorithmic HBM bytes per walker of the layer + orbital GEMMs of one
+    local-energy pass: every operand and result crossing HBM once, with the
+    real tangent columns (C = 3n + 2) and features only.  Activations, spin
+    means and U count 4 bytes an element (BF16 hi + lo, or FP32); orbitals
+    count the same-spin blocks only (FP32)."""
+    n, N, d1, d2, K, L = net.n_elec, net.n_nuc, net.d1, net.d2, net.n_det, net.n_layers
+    C = 3 * n + 2
+    R = n * C  # rows of one walker
+    tot = 0.0
+    for l in range(L):
+        a1 = 4 * N if l == 0 else d1
+        a2 = 4 if l == 0 else d2
+        tot += 4.0 * (C * 2 * a1 + C * d1)                    # U GEMM: spin means in, U out
+        tot += 4.0 * (R * a1 + R * 2 * a2 + C * d1 + R * d1)  # layer: h, pair means, U in; h' out
+    tot += 4.0 * (R * d1 + (net.n_up ** 2 + net.n_down ** 2) * K * C)  # orbitals
+    return tot
+
+
+def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_launch=None, net=None):
     r = fn.profile_read("tangent_gemm")
     if r["launches"] == 0 or r["ms"] <= 0:
         return None
@@ -233,10 +252,19 @@ def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_l
         bound, note = "tensor", f"bf16 sustained, {pk_kind}"
     bpw = recorded_traffic(workload, prec) if workload else None
     traffic = bpw * walkers_per_launch if (bpw is not None and walkers_per_launch) else None
+    hbm = None
+    if net is not None and walkers_per_launch:
+        hpk = _num(pk, "hbm_gbs") or 6800.0
+        gbs = gemm_class_alg_bytes(net) * walkers_per_launch / (r["ms"] / r["launches"] * 1e-3) / 1e9
+        hbm = {"achieved": gbs, "peak": hpk, "unit": "GB/s", "frac": gbs / hpk,
+               "bytes_per_walker": gemm_class_alg_bytes(net),
+               "note": "algorithmic bytes (real columns and features, once) over the same launches; "
+                       f"copy peak, {pk_kind}"}
     return {"bound": bound, "kernel": "layer + orbital GEMMs of the local-energy pass", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
             "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-            "launches": r["launches"], "avg_launch_ms": r["ms"] / r["launches"], "peak_note": note}
+            "launches": r["launches"], "avg_launch_ms": r["ms"] / r["launches"], "peak_note": note,
+            "hbm_view": hbm}
 
 
 def run_gpu(args, wl):
@@ -313,7 +341,7 @@ def run_gpu(args, wl):
     passes = args.steps  # one local-energy pass per step
     launches_per_pass = max(1, r_tg["launches"] // max(passes, 1))
     roof = tangent_roofline(fn, prec, clocks, pk, pk_kind, wl.name,
-                            wl.batch * passes / max(r_tg["launches"], 1))
+                            wl.batch * passes / max(r_tg["launches"], 1), net=wl.net)
     classes = {k: fn.profile_read(k) for k in ("tangent_gemm", "det_tangent", "two_layer", "means", "tanh",
                                                  "value_pass", "adjoint")}
     fn.profile(False)
