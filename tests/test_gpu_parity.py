@@ -340,9 +340,10 @@ def test_two_electron_width_outside_fused_kernel():
 
 @pytest.mark.parametrize("env", [{"FERMINET_PIVOT_TAU": "0.999"}, {"FERMINET_DET64": "1"}])
 def test_fp64_determinant_redo(monkeypatch, env):
-    """Every orbital matrix goes through the FP64 redo of the tangent pass
-    (flagged by the pivot ratio, or forced): E_L still matches the oracle,
-    and the flagged count reports the matrices when flagging is by ratio."""
+    """Every orbital matrix goes through the FP64 redo (flagged by the pivot
+    ratio, or forced), in the tangent pass and in the value pass: E_L and
+    log|psi| still match the oracle, and the flagged count reports the matrices
+    when flagging is by ratio."""
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     wl, lay, P, x, geo = setup("c4h6", 3)
@@ -354,6 +355,11 @@ def test_fp64_determinant_redo(monkeypatch, env):
     bound = eloc_bound(wl.net, ref)
     assert np.all(de <= bound), (de / bound).max()
     assert np.all(np.abs(out["logpsi"].cpu().numpy() - ref["logpsi"]) <= logpsi_bound(wl.net, ref))
+    # the value pass takes the same route (its pairs redone by the list kernel)
+    lp, sg = fn.logpsi(cuda(x))
+    assert fn.sync() == "FN_OK"
+    assert np.all(np.abs(lp.cpu().numpy() - ref["logpsi"]) <= logpsi_bound(wl.net, ref))
+    assert np.array_equal(sg.cpu().numpy(), ref["sign"])
     if "FERMINET_PIVOT_TAU" in env:
         fn.local_energy(cuda(x))
         assert fn.flagged_matrices() > 0
