@@ -166,6 +166,8 @@ struct DetArgs {
                        // pairs (value pass) to redo in FP64
 };
 void launch_det(cudaStream_t s, const DetArgs& a);
+void launch_det_tangent(cudaStream_t s, const DetArgs& a);     // k_det_tangent.cu (called by launch_det)
+void launch_det_value_warp(cudaStream_t s, const DetArgs& a);  // k_det_value.cu (called by launch_det)
 
 // ---------------------------------------------------------------------------
 // Energies, Metropolis, reductions (k_energy.cu)
