@@ -25,7 +25,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "VMC walker-steps/sec (psi, E_L, grad) vs plain FP32 path at stated error"
 UNIT = "walker-steps/s"
-DEFAULT_WORKLOAD = "c4h6"
+DEFAULT_WORKLOAD = "c4h4x8"
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
 
 
@@ -153,6 +153,9 @@ def run_reference(args, wl):
     import numpy as np
     import oracle
     from paper_2011_07125_gb300 import synth
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # under a rank launcher (which sets one thread per rank) rank 0 runs alone
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     cores = int(os.environ["OMP_NUM_THREADS"])
     lay = oracle.layout(wl.net)
@@ -244,9 +247,12 @@ def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_l
         return None
     achieved = r["alg_flops"] / (r["ms"] * 1e-3) / 1e12
     if prec == "fp32":
+        import torch
         mhz = clocks.get("sm_max_mhz") or 2070.0
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-        bound, note = "alu", f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz"
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        bound, note = "alu", (f"FP32 FMA peak: {sms} SMs (from the device) x 128 FP32 lanes x 2 flops x "
+                              f"{mhz:.0f} MHz (maximum SM clock seen)")
     else:
         peak = _num(pk, "bf16_tflops_sustained", "bf16_tflops") or 1700.0
         bound, note = "tensor", f"bf16 sustained, {pk_kind}"
@@ -265,6 +271,129 @@ def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_l
             "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
             "launches": r["launches"], "avg_launch_ms": r["ms"] / r["launches"], "peak_note": note,
             "hbm_view": hbm}
+
+
+def geometry_sample(wl, per_geom: int):
+    """Indices of `per_geom` walkers of every geometry, spread over its range."""
+    import numpy as np
+    idx, off = [], 0
+    for c in wl.counts:
+        k = min(per_geom, c)
+        idx.extend(off + np.linspace(0, c - 1, k).astype(int))
+        off += c
+    return np.array(idx, np.int64)
+
+
+def error_report(wl, P, xs, geo, eloc, logpsi, prec, grad_fn=None):
+    """Errors of the GPU results on sampled walkers against the FP64 oracle:
+    per-geometry batch-mean E_L error, per-walker E_L and log|psi| errors with
+    the fraction inside the FP32 bars (1e-4 Ha, 1e-5 relative), and, when
+    grad_fn is given, the VMC gradient's relative L2 error (grad_fn(ref_eloc)
+    returns the GPU gradient on the same walkers)."""
+    import numpy as np
+    import oracle
+    ref = oracle.local_energy(wl.net, P, wl.geoms, xs, geo=geo)
+    de = eloc.astype(np.float64) - ref["eloc"]
+    dl = np.abs(logpsi.astype(np.float64) - ref["logpsi"]) / np.maximum(np.abs(ref["logpsi"]), 1.0)
+    per_geo = [float(de[geo == g].mean()) for g in range(len(wl.geoms)) if np.any(geo == g)]
+    rep = {"walkers": int(len(xs)), "eloc_mean_err_per_geometry": per_geo,
+           "eloc_mean_err_max_abs": float(np.max(np.abs(per_geo))),
+           "eloc_max_abs": float(np.abs(de).max()), "eloc_median_abs": float(np.median(np.abs(de))),
+           "frac_eloc_within_1e-4": float(np.mean(np.abs(de) <= 1e-4)),
+           "logpsi_max_rel": float(dl.max()), "frac_logpsi_within_1e-5": float(np.mean(dl <= 1e-5)),
+           "bar": ("batch-mean E_L within 1e-3 Ha" if prec == "mixed" else
+                   "1e-5 relative log|psi|, 1e-4 Ha per walker, 1e-5 Ha batch mean")}
+    if grad_fn is not None:
+        _, g_o = oracle.energy_grad(wl.net, P, wl.geoms, xs, ref["eloc"], geo=geo)
+        g = grad_fn()
+        rep["grad_rel_l2"] = float(np.linalg.norm(g - g_o) / np.linalg.norm(g_o))
+    return rep
+
+
+def sample_context_grad(wl, prec, params, xs_np, counts):
+    """VMC gradient of the GPU path on the sampled walkers alone (a context
+    whose geometry table holds the sample's counts)."""
+    import numpy as np
+    import torch
+    from paper_2011_07125_gb300.binding import FermiNet
+    f = FermiNet(wl.net, wl.geoms, counts=counts, precision=prec)
+    f.set_params(params)
+    xx = torch.from_numpy(np.ascontiguousarray(xs_np)).cuda()
+    e = f.local_energy(xx)["eloc"]
+    _, g = f.energy_grad(xx, e)
+    out = g.cpu().numpy().astype(np.float64)
+    f.close()
+    return out
+
+
+def timed_steps(fn, wl, x, lp, steps, warmup, flush, grad_of, counter0=0):
+    """Runs `warmup` then `steps` VMC steps (moves, E_L, gradient) on the
+    context stream; returns (per-step ms list, last local-energy output)."""
+    import torch
+    from paper_2011_07125_gb300 import synth
+    counter = [counter0]
+    s = torch.cuda.current_stream()
+
+    def step():
+        fn.mcmc_step(x, lp, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, counter[0])
+        counter[0] += wl.mcmc_steps
+        out = fn.local_energy(x)
+        grad_of(fn, x, out["eloc"])
+        return out
+
+    out = None
+    for _ in range(warmup):
+        out = step()
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))  # L2 flush outside the timed events
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        out = step()
+        b.record(s)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ms], out
+
+
+def side_workload(name, flush, args):
+    """A shorter measurement of another workload in the same run: its own
+    precision (and the other one for comparison), and its error against the
+    oracle on sampled walkers."""
+    import numpy as np
+    import torch
+    from paper_2011_07125_gb300 import synth
+    from paper_2011_07125_gb300.binding import FermiNet
+    wl = synth.workload(name)
+    res = {"workload": describe(wl), "precision": wl.precision}
+    x0 = synth.init_walkers(wl)
+    P = None
+    for prec in (wl.precision, "fp32" if wl.precision == "mixed" else "mixed"):
+        fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision=prec)
+        if P is None:
+            P = synth.init_params(fn.layout)
+            params = torch.from_numpy(P).cuda()
+        fn.set_params(params)
+        x = torch.from_numpy(x0).cuda()
+        lp = fn.logpsi(x, with_sign=False)
+        if prec == "mixed" and not args.no_autotune:
+            fn.autotune_cached(x, repeats=1)
+        ms, out = timed_steps(fn, wl, x, lp, 3, 2, flush, lambda f, xx, e: f.energy_grad(xx, e))
+        st = fn.sync()
+        v = wl.batch * len(ms) / (sum(ms) * 1e-3)
+        res[prec] = {"value": v, "unit": UNIT, "ms_per_step": sum(ms) / len(ms), "status": st}
+        if prec == wl.precision and not args.no_cpu_baseline:
+            idx = geometry_sample(wl, 32 if prec == "fp32" else 16)
+            xs = np.ascontiguousarray(x.cpu().numpy()[idx])
+            geo = synth.geometry_of_walkers(wl.counts)[idx]
+            res["error_vs_oracle"] = error_report(
+                wl, P, xs, geo, out["eloc"].cpu().numpy()[idx], out["logpsi"].cpu().numpy()[idx], prec,
+                grad_fn=lambda: sample_context_grad(wl, prec, params, xs, [len(xs)]))
+        fn.close()
+    if "fp32" in res and "mixed" in res:
+        res["mixed_over_fp32"] = res["mixed"]["value"] / res["fp32"]["value"]
+    return res
 
 
 def run_gpu(args, wl):
@@ -339,7 +468,6 @@ def run_gpu(args, wl):
     pk, pk_kind = peaks()
     r_tg = fn.profile_read("tangent_gemm")
     passes = args.steps  # one local-energy pass per step
-    launches_per_pass = max(1, r_tg["launches"] // max(passes, 1))
     roof = tangent_roofline(fn, prec, clocks, pk, pk_kind, wl.name,
                             wl.batch * passes / max(r_tg["launches"], 1), net=wl.net)
     classes = {k: fn.profile_read(k) for k in ("tangent_gemm", "det_tangent", "two_layer", "means", "tanh",
@@ -347,6 +475,10 @@ def run_gpu(args, wl):
     fn.profile(False)
     ms_per_step = ms / args.steps
     value = world * wl.batch * args.steps / (ms * 1e-3)
+    # positions and local energies of the last timed step, for the error report
+    x_last = x.clone()
+    eloc_last = out["eloc"].cpu().numpy()
+    logpsi_last = out["logpsi"].cpu().numpy()
 
     # plain FP32 path on the same workload (the metric's comparison), when the timed path is mixed
     fp32 = None
@@ -355,28 +487,11 @@ def run_gpu(args, wl):
         f32.set_params(params)
         xs = torch.from_numpy(x0).to(dev)
         lps = f32.logpsi(xs, with_sign=False)
-        c2 = [0]
-
-        def step32():
-            f32.mcmc_step(xs, lps, wl.mcmc_steps, wl.mcmc_width, synth.SEED_MCMC, c2[0])
-            c2[0] += wl.mcmc_steps
-            o = f32.local_energy(xs)
-            f32.energy_grad(xs, o["eloc"])
-
-        for _ in range(max(1, args.warmup // 2)):
-            step32()
-        torch.cuda.synchronize()
-        t32 = 0.0
-        for k in range(max(2, args.steps // 2)):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(s)
-            step32()
-            b.record(s)
-            torch.cuda.synchronize()
-            t32 += a.elapsed_time(b)
-        n32 = max(2, args.steps // 2)
-        fp32 = {"value": wl.batch * n32 / (t32 * 1e-3), "unit": UNIT, "ms_per_step": t32 / n32}
+        n32 = max(2, min(args.steps // 2, 4))
+        t32, _ = timed_steps(f32, wl, xs, lps, n32, max(1, min(args.warmup // 2, 2)), flush,
+                             lambda f, xx, e: f.energy_grad(xx, e))
+        fp32 = {"value": wl.batch * n32 / (sum(t32) * 1e-3), "unit": UNIT, "ms_per_step": sum(t32) / n32,
+                "status": f32.sync()}
         f32.close()
 
     # end to end through the public API (ferminet_step, replayed from its CUDA
@@ -432,46 +547,91 @@ def run_gpu(args, wl):
                                      mh.numel() * 8),
            "api": "ferminet_step (CUDA graph replay)" if world == 1 else
                   "ferminet_mcmc_step + ferminet_local_energy + two-phase gradient all-reduce"}
+    e2e_status = fn.sync()
+    fn.close()
 
     cpu = None
     err = None
-    if rank == 0 and not args.no_cpu_baseline:
+    side = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
-        import oracle
-        xs_np = x.cpu().numpy().astype(np.float32)
+        xs_np = x_last.cpu().numpy().astype(np.float32)
         S = cpu_sample_size(wl, P, xs_np, 15.0)
-        xs_np = xs_np[:S]
-        dt, eloc_o, _ = oracle_step_sample(wl, P, xs_np, 0)
+        dt, _, _ = oracle_step_sample(wl, P, xs_np[:S], 0)
         cpu = {"value": S / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
                "sample": f"{S} walkers of the {wl.batch}-walker batch ({wl.mcmc_steps} moves + E_L + gradient), "
                          f"{dt:.1f} s"}
-        # error of the timed path on the same sampled walkers (current positions)
-        o = fn.local_energy(x[:S].contiguous()) if len(wl.geoms) == 1 else None
-        if o is not None:
-            ref = oracle.local_energy(wl.net, P, wl.geoms[:1], xs_np)
-            de = np.abs(o["eloc"].cpu().numpy() - ref["eloc"])
-            err = {"walkers": S, "eloc_max_abs": float(de.max()), "eloc_median_abs": float(np.median(de)),
-                   "eloc_mean_err": float(abs(o["eloc"].cpu().numpy().mean() - ref["eloc"].mean())),
-                   "logpsi_max_rel": float((np.abs(o["logpsi"].cpu().numpy() - ref["logpsi"]) /
-                                            np.maximum(np.abs(ref["logpsi"]), 1)).max())}
+        # error of the timed path on walkers sampled from every geometry (the
+        # positions and local energies of the last timed step)
+        idx = geometry_sample(wl, args.err_per_geom)
+        geo = synth.geometry_of_walkers(wl.counts)[idx]
+        xs = np.ascontiguousarray(xs_np[idx])
+        cnt = [int((geo == g).sum()) for g in range(len(wl.geoms))]
+        err = error_report(wl, P, xs, geo, eloc_last[idx], logpsi_last[idx], prec,
+                           grad_fn=lambda: sample_context_grad(wl, prec, params, xs, cnt))
+    if rank == 0 and world == 1 and args.side:
+        for name in args.side.split(","):
+            if name and name != wl.name:
+                side[name] = side_workload(name, flush, args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16/f32",
                 "data": "synthetic (seeded walkers, N(0,1/fan_in) weights; the paper ships no data)",
-                "config": {"workload": describe(wl), "walkers": wl.batch, "precision": prec,
+                "config": {"workload": describe(wl), "walkers": wl.batch, "walkers_per_geometry": wl.counts,
+                           "precision": prec,
                            "l2": "256 MiB buffer written between timed steps, outside the timed events",
                            "parallelism": f"data parallel over walkers x{world} (all-reduce of energy sums and "
                                           f"FP64 gradient shares)" if world > 1 else "single GPU",
                            "tuning": tuning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "status": st, "fp32_path": fp32, "error_vs_oracle": err,
-                "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in classes.items()}}
+                "clocks": clocks, "status": st, "e2e_status": e2e_status, "fp32_path": fp32,
+                "mixed_over_fp32": (value / fp32["value"]) if fp32 else None,
+                "error_vs_oracle": err,
+                "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in classes.items()},
+                "other_workloads": side or None}
         print(json.dumps(line), flush=True)
-    fn.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def check_launch(args):
+    """Host-only check of the rank launch (gloo): every rank joins, rank 0
+    prints the world size and the ranks that answered."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    t = torch.zeros(max(world, 1), dtype=torch.int64)
+    t[rank] = rank + 1
+    if world > 1:
+        dist.all_reduce(t)
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps({"check_launch": True, "n_gpus": world, "ranks": [int(v) - 1 for v in t.tolist()]}),
+              flush=True)
+
+
+def _free_port() -> int:
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    return port
+
+
+def launch_ranks(args) -> None:
+    """--gpus N > 1 without a launcher: start N ranks on this node through
+    torch.distributed.run (one process per GPU) and exit with its status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__),
+           *sys.argv[1:]]
+    sys.stdout.flush()
+    os.execv(sys.executable, cmd)
 
 
 def main():
@@ -482,10 +642,28 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "mixed"])
+    ap.add_argument("--side", default=None,
+                    help="comma-separated workloads measured briefly after the main one (default: ne,ar with the "
+                         "default workload, none otherwise)")
+    ap.add_argument("--err-per-geom", type=int, default=6, help="walkers per geometry in the oracle error check")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--check-launch", action="store_true", help="host-only check of the rank launch, then exit")
     args = ap.parse_args()
+    if args.side is None:
+        args.side = "ne,ar" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours" else ""
+    if args.gpus < 1:
+        sys.exit("--gpus must be at least 1")
+    world = os.environ.get("WORLD_SIZE")
+    if world is None and args.gpus > 1 and args.impl == "ours":
+        launch_ranks(args)
+        return
+    if world is not None and int(world) != args.gpus:
+        sys.exit(f"--gpus {args.gpus} but the launcher started {world} ranks")
+    if args.check_launch:
+        check_launch(args)
+        return
     from paper_2011_07125_gb300 import synth
     wl = synth.workload(args.workload)
     if args.impl == "reference":

@@ -133,7 +133,11 @@ fn_status ferminet_set_params(fn_ctx* ctx, const float* d_params);
  * All calls share the one array and each call rewrites what it reads, but two
  * calls whose work overlaps on the GPU (different streams, or different host
  * threads on the same device) race on it: serialise them.  Ill-conditioning
- * and singularity counters are cleared at every call and are not reported. */
+ * and singularity counters are cleared at every call and are not reported.
+ * The FP64 redo follows the same environment settings as ferminet_init
+ * (FERMINET_PIVOT_TAU, FERMINET_DET64).  FN_ECUDA reports a failed launch of
+ * this call; a CUDA error already pending on the calling thread is left in
+ * place and not reported. */
 fn_status ferminet_logpsi_noalloc(const fn_net* net, const float* d_params, const float* d_R, const float* d_x,
                                   long B, float* d_logpsi, float* d_sign, void* stream);
 
@@ -166,19 +170,24 @@ fn_status ferminet_energy_grad(fn_ctx* ctx, const float* d_x, long B, const floa
  * E_L,w minus the mean over the whole batch, so it takes two exchanges:
  *   1. ferminet_energy_sums: d_sums [n_geoms] (double) = FP64 sum of d_eloc
  *      over this process's walkers of each geometry.  The caller adds d_sums
- *      and the walker counts over the processes and divides (E_mean,g).
- *   2. ferminet_energy_grad_partial: d_grad64 [n_params] (double) =
- *      sum_g 2/count_g sum_{w of g here} (E_L,w - d_emean[g]) d log|psi_w|/d theta,
- *      with d_emean and d_count [n_geoms] (double) over the whole batch,
- *      accumulated in FP64.  The sum of d_grad64 over the processes is the
- *      gradient ferminet_energy_grad computes on the whole batch.
+ *      and the walker counts over the processes (an all-reduce).
+ *   2. ferminet_energy_grad_partial: with d_esum and d_count [n_geoms]
+ *      (double) the energy sums and walker counts over the whole batch, the
+ *      library forms E_mean,g = d_esum[g] / d_count[g] in FP64 on the device
+ *      (stored into d_emean [n_geoms] when it is not NULL) and accumulates
+ *      d_grad64 [n_params] (double) =
+ *      sum_g 2/count_g sum_{w of g here} (E_L,w - E_mean,g) d log|psi_w|/d theta
+ *      in FP64.  The sum of d_grad64 over the processes is the gradient
+ *      ferminet_energy_grad computes on the whole batch.
  * With one process (count_g = this batch's) the two calls reproduce
- * ferminet_energy_grad.  A geometry with walkers here must have count_g > 0.
+ * ferminet_energy_grad.  A geometry with walkers here must have count_g > 0
+ * (E_mean,g of a geometry with count_g = 0 is stored as 0).
  * B follows the rules of ferminet_energy_grad (with several geometries, B
  * equals the walker total of the geometry table). */
 fn_status ferminet_energy_sums(fn_ctx* ctx, const float* d_eloc, long B, double* d_sums);
 fn_status ferminet_energy_grad_partial(fn_ctx* ctx, const float* d_x, long B, const float* d_eloc,
-                                       const double* d_emean, const double* d_count, double* d_grad64);
+                                       const double* d_esum, const double* d_count, double* d_emean,
+                                       double* d_grad64);
 
 /* n_steps Gaussian all-electron Metropolis moves sampling |psi|^2 (Eq. 2).
  * Step s uses counter t = counter + s.  For walker w the proposal is

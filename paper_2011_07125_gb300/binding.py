@@ -92,7 +92,7 @@ def load(path: Optional[str] = None):
         lib.ferminet_logpsi_vjp.argtypes = [vp, vp, C.c_long, vp, vp]
         lib.ferminet_energy_grad.argtypes = [vp, vp, C.c_long, vp, vp, vp]
         lib.ferminet_energy_sums.argtypes = [vp, vp, C.c_long, vp]
-        lib.ferminet_energy_grad_partial.argtypes = [vp, vp, C.c_long, vp, vp, vp, vp]
+        lib.ferminet_energy_grad_partial.argtypes = [vp, vp, C.c_long, vp, vp, vp, vp, vp]
         lib.ferminet_mcmc_step.argtypes = [vp, vp, vp, C.c_long, C.c_int, C.c_float, C.c_uint64, C.c_uint64, vp]
         lib.ferminet_step.argtypes = [vp, vp, vp, C.c_long, C.c_int, C.c_float, C.c_uint64, C.c_uint64, vp, vp, vp,
                                       vp, C.c_int]
@@ -255,19 +255,22 @@ class FermiNet:
         self._check(self.lib.ferminet_energy_sums(self.ctx, _ptr(eloc), B, _ptr(s)), "ferminet_energy_sums")
         return s
 
-    def energy_grad_partial(self, x, eloc, emean, count):
-        """This process's share of the VMC gradient given the mean energy and
-        walker count of every geometry over the whole batch (float64 [P])."""
+    def energy_grad_partial(self, x, eloc, esum, count):
+        """This process's share of the VMC gradient given the energy sum and
+        walker count of every geometry over the whole batch.  The library
+        divides them (FP64, on the GPU).  Returns (emean [G], grad [P]), both
+        float64."""
         B = x.shape[0]
         self._f32(x, (B, self.n, 3))
         self._f32(eloc, (B,))
-        for t in (emean, count):
+        for t in (esum, count):
             if not (t.is_cuda and t.dtype == self.torch.float64 and t.is_contiguous() and t.numel() == self.G):
                 raise FermiNetError(f"expected a contiguous float64 CUDA tensor of {self.G} elements")
+        em = self._empty(self.G, dtype=self.torch.float64)
         g = self._empty(self.n_params, dtype=self.torch.float64)
-        self._check(self.lib.ferminet_energy_grad_partial(self.ctx, _ptr(x), B, _ptr(eloc), _ptr(emean), _ptr(count),
-                                                          _ptr(g)), "ferminet_energy_grad_partial")
-        return g
+        self._check(self.lib.ferminet_energy_grad_partial(self.ctx, _ptr(x), B, _ptr(eloc), _ptr(esum), _ptr(count),
+                                                          _ptr(em), _ptr(g)), "ferminet_energy_grad_partial")
+        return em, g
 
     def mcmc_step(self, x, logpsi, n_steps, width, seed, counter, accepted=None):
         """Advances x and logpsi in place; returns the accepted-move counts."""

@@ -23,18 +23,20 @@ namespace fn {
 
 std::atomic<long long> g_launches{0};
 
-void build_layout(const fn_net& t, Layout* L) {
+void build_layout(const fn_net& t, Layout* L, bool with_entries) {
   L->entries.clear();
   long off = 0;
   auto add = [&](long* field, const char* nm, long cnt, long fan, int kind) {
     if (field) *field = off;
-    fn_param_entry e{};
-    snprintf(e.name, sizeof e.name, "%s", nm);
-    e.offset = off;
-    e.count = cnt;
-    e.fan_in = fan;
-    e.kind = kind;
-    L->entries.push_back(e);
+    if (with_entries) {
+      fn_param_entry e{};
+      snprintf(e.name, sizeof e.name, "%s", nm);
+      e.offset = off;
+      e.count = cnt;
+      e.fan_in = fan;
+      e.kind = kind;
+      L->entries.push_back(e);
+    }
     off += cnt;
   };
   char nm[32];
@@ -763,16 +765,22 @@ size_t ws_bytes(fn_ctx* c, long Bc, int mode) {
 // Workspace budget: 30% of the device's memory, at most 80 GB (GB300: the
 // whole 4096-walker local-energy pass in one chunk); FERMINET_WS_GB overrides.
 double default_ws_gb() {
-  static double gb = -1.0;
-  if (gb < 0.0) {
+  static double gb[kMaxDevices];
+  static PerDeviceOnce once;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) {
+    cudaGetLastError();
+    return 24.0;
+  }
+  once([&] {
     size_t freeb = 0, total = 0;
-    gb = 24.0;
+    gb[d] = 24.0;
     if (cudaMemGetInfo(&freeb, &total) == cudaSuccess && total > 0)
-      gb = std::min(80.0, 0.3 * (double)total / (double)(1ull << 30));
+      gb[d] = std::min(80.0, 0.3 * (double)total / (double)(1ull << 30));
     else
       cudaGetLastError();
-  }
-  return gb;
+  });
+  return gb[d];
 }
 
 // Largest chunk whose workspace fits the budget.
@@ -894,6 +902,25 @@ fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* 
 
 namespace fn {
 
+int device_sm_count() {
+  static int n[kMaxDevices];
+  static PerDeviceOnce once;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) {
+    cudaGetLastError();
+    return 148;
+  }
+  once([&] {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 148;
+    }
+    n[d] = v;
+  });
+  return n[d];
+}
+
 // Value pass over B walkers of one geometry with a caller-supplied workspace
 // and no allocation of any kind (host or device).  The first 256 bytes of ws
 // hold the status and flag words; the rest is cut into walker chunks.
@@ -908,35 +935,11 @@ fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, c
   c.Ct = tangent_cols(c.n);
   c.stream = s;
   c.ns_max = std::max(net.n_up, net.n_down);
-  // parameter offsets (same order as build_layout, computed without the entry table)
-  long off = 0;
-  for (int l = 0; l < net.n_layers; ++l) {
-    const long a = din1_of(net, l), e = din2_of(net, l);
-    c.lay.V[l] = off;
-    off += (long)net.d1 * (3 * a + 2 * e);
-    c.lay.b[l] = off;
-    off += net.d1;
-    if (l < net.n_layers - 1) {
-      c.lay.W[l] = off;
-      off += (long)net.d2 * e;
-      c.lay.c[l] = off;
-      off += net.d2;
-    }
-  }
-  const long K = net.n_det;
-  c.lay.w_orb = off;
-  off += K * c.n * net.d1;
-  c.lay.g_orb = off;
-  off += K * c.n;
-  c.lay.pi[0] = off;
-  off += K * net.n_up * net.n_nuc;
-  c.lay.pi[1] = off;
-  off += K * net.n_down * net.n_nuc;
-  c.lay.sigma[0] = off;
-  off += K * net.n_up * net.n_nuc;
-  c.lay.sigma[1] = off;
-  off += K * net.n_down * net.n_nuc;
-  c.lay.total = off;
+  // parameter offsets only: the entry table (host memory) is not built
+  build_layout(net, &c.lay, false);
+  // the FP64 redo settings of ferminet_init
+  if (const char* v = getenv("FERMINET_PIVOT_TAU")) c.pivot_tau = (float)atof(v);
+  if (const char* v = getenv("FERMINET_DET64")) c.force64 = atoi(v) != 0;
   c.d_params = const_cast<float*>(d_params);
   c.d_R = const_cast<float*>(d_R);
   c.d_status = reinterpret_cast<unsigned*>(ws);
@@ -951,6 +954,9 @@ fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, c
   if (ch < 1) ch = 1;
   while (ch > 1 && ws_bytes(&c, ch, 0) > avail) --ch;
   if (ch > B) ch = B;
+  // launch errors of this call: an error already pending on this thread
+  // belongs to earlier work and is left in place
+  const cudaError_t prior = cudaPeekAtLastError();
   if (cudaMemsetAsync(ws, 0, head, s) != cudaSuccess) return FN_ECUDA;
   const long n3 = 3L * c.n;
   for (long w0 = 0; w0 < B; w0 += ch) {
@@ -963,7 +969,10 @@ fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, c
     o.sign = d_sign ? d_sign + w0 : nullptr;
     forward(&c, ar, d_x + w0 * n3, Bc, w0, false, false, o, nullptr);
   }
-  return cudaGetLastError() == cudaSuccess ? FN_OK : FN_ECUDA;
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess || e == prior) return FN_OK;
+  cudaGetLastError();  // this call's own launch error
+  return FN_ECUDA;
 }
 
 }  // namespace fn
@@ -1240,16 +1249,17 @@ fn_status ferminet_energy_sums(fn_ctx* c, const float* d_eloc, long B, double* d
 }
 
 fn_status ferminet_energy_grad_partial(fn_ctx* c, const float* d_x, long B, const float* d_eloc,
-                                       const double* d_emean, const double* d_count, double* d_grad64) {
+                                       const double* d_esum, const double* d_count, double* d_emean,
+                                       double* d_grad64) {
   if (!c) return FN_EINVAL;
   fn_status st = check_batch(c, d_x, B);
   if (st != FN_OK) return st;
-  if (!d_grad64 || !d_emean || !d_count || (!d_eloc && B > 0))
-    return fail(c, FN_EINVAL, "null eloc, emean, count or grad pointer");
+  if (!d_grad64 || !d_esum || !d_count || (!d_eloc && B > 0))
+    return fail(c, FN_EINVAL, "null eloc, energy sum, count or grad pointer");
   st = ensure_aux(c, std::max<long>(B, 1));
   if (st != FN_OK) return st;
   float* seeds = c->aux;
-  launch_seeds_given(c->stream, d_eloc, B, c->G > 1 ? c->d_geo : nullptr, d_emean, d_count, seeds);
+  launch_seeds_given(c->stream, d_eloc, B, c->G > 1 ? c->d_geo : nullptr, d_esum, d_count, c->G, d_emean, seeds);
   return run_vjp(c, d_x, B, seeds, nullptr, d_grad64);
 }
 

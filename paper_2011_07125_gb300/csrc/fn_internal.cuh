@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,36 @@ inline int tangent_cols(int n) { return ((3 * n + 2 + 7) / 8) * 8; }
 // coordinates; Q = 1 in the value pass.
 constexpr int kQ = 5;
 
+// Per-device state.  Kernel attributes (the dynamic shared-memory limit) and
+// device properties belong to one device, and one process may drive several,
+// so everything the library sets up once is set up once per device: the
+// device current at the call.
+constexpr int kMaxDevices = 64;
+class PerDeviceOnce {
+ public:
+  template <class F>
+  void operator()(F&& f) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) {
+      cudaGetLastError();
+      f();
+      return;
+    }
+    if (done_[d].load(std::memory_order_acquire)) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    if (!done_[d].load(std::memory_order_relaxed)) {
+      f();
+      done_[d].store(true, std::memory_order_release);
+    }
+  }
+
+ private:
+  std::atomic<bool> done_[kMaxDevices] = {};
+  std::mutex mu_;
+};
+// Multiprocessor count of the current device (cached per device).
+int device_sm_count();
+
 // Kernels launched by the library (every launch site adds one).
 extern std::atomic<long long> g_launches;
 #define FN_COUNT(n) (::fn::g_launches.fetch_add((n), std::memory_order_relaxed))
@@ -40,7 +71,8 @@ struct Layout {
   long total;
   std::vector<fn_param_entry> entries;
 };
-void build_layout(const fn_net& t, Layout* L);
+// with_entries = false fills the offsets only and allocates nothing.
+void build_layout(const fn_net& t, Layout* L, bool with_entries = true);
 
 inline int din1_of(const fn_net& t, int l) { return l == 0 ? 4 * t.n_nuc : t.d1; }
 inline int din2_of(const fn_net& t, int l) { return l == 0 ? 4 : t.d2; }
@@ -182,16 +214,18 @@ void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, con
 void launch_set_u64(cudaStream_t s, uint64_t* p, uint64_t v);
 // With G == 1 the single geometry holds all B walkers (B1 = B >= 0); with
 // B1 < 0 the device tables d_off / d_cnt give each geometry's walker range.
-// launch_esum writes sums instead of means; launch_seeds_given takes the mean
-// and the walker count of every geometry over the whole (replicated) batch.
+// launch_esum writes sums instead of means; launch_seeds_given takes the
+// energy sum and the walker count of every geometry over the whole
+// (replicated) batch, divides them in FP64 and stores the means in emean
+// (when not null).
 void launch_emean(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
                   double* emean);
 void launch_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
                   const long* d_cnt, long B1, float* seeds);
 void launch_esum(cudaStream_t s, const float* eloc, int G, const long* d_off, const long* d_cnt, long B1,
                  double* sums);
-void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
-                        const double* count, float* seeds);
+void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* sums,
+                        const double* count, int G, double* emean, float* seeds);
 void launch_d2f(cudaStream_t s, const double* a, float* b, long n);
 void launch_fill(cudaStream_t s, float* p, float v, long n);
 void launch_zero_d(cudaStream_t s, double* p, long n);

@@ -178,7 +178,7 @@ void launch_value_nm(cudaStream_t s, const DetArgs& a) {
     const size_t sm = sizeof(float) * 4 * a.n * a.N;
     cudaMemsetAsync(a.redo, 0, sizeof(int), s);  // empty redo list
     FN_COUNT(1), k_det_value_pair<NM <= 16 ? NM : 16><<<(unsigned)((npair + 3) / 4), 128, sm, s>>>(a);
-    const long redo_blocks = std::min<long>((npair + 3) / 4, 152L * 2);
+    const long redo_blocks = std::min<long>((npair + 3) / 4, 2L * device_sm_count());
     FN_COUNT(1), k_det_value_pair_redo<NM <= 16 ? NM : 16><<<(unsigned)redo_blocks, 128, sm, s>>>(a);
   } else {
     launch_det_value_warp(s, a);

@@ -257,15 +257,14 @@ void launch_tangent_nm(cudaStream_t s, const DetArgs& a) {
   if (nmat <= 0) return;
   const int smem = (int)sizeof(TangentSmem<NM, float>);
   const int smem64 = (int)sizeof(TangentSmem<NM, double>);
-  static bool attr = false;  // set once per process (the attribute is per function)
-  if (!attr) {
+  static PerDeviceOnce attr;  // the attribute is per function and device
+  attr([&] {
     cudaFuncSetAttribute(k_det_tangent<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_det_tangent_redo<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
-    attr = true;
-  }
+  });
   cudaMemsetAsync(a.redo, 0, sizeof(int), s);  // empty redo list
   FN_COUNT(1), k_det_tangent<NM><<<(unsigned)nmat, 128, smem, s>>>(a);
-  const long redo_blocks = std::min<long>(nmat, 152L * 2);
+  const long redo_blocks = std::min<long>(nmat, 2L * device_sm_count());
   FN_COUNT(1), k_det_tangent_redo<NM><<<(unsigned)redo_blocks, 128, smem64, s>>>(a);
 }
 

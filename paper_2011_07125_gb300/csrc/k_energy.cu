@@ -3,6 +3,8 @@
 // reductions of the VMC gradient.
 #include <math.h>
 
+#include <algorithm>
+
 #include "fn_internal.cuh"
 
 namespace fn {
@@ -206,14 +208,18 @@ __global__ void k_seeds(const float* __restrict__ eloc, long B, const int* __res
   seeds[w] = (float)(2.0 * ((double)eloc[w] - emean[g]) / c);
 }
 
-// Seeds of the replica form: the mean and the count are those of the whole
-// batch over all replicas.
+// Seeds of the replica form: the energy sum and the walker count of every
+// geometry over the whole batch (all replicas) give its mean in FP64; threads
+// w < G also store that mean.
 __global__ void k_seeds_given(const float* __restrict__ eloc, long B, const int* __restrict__ geo,
-                              const double* __restrict__ emean, const double* __restrict__ count, float* seeds) {
+                              const double* __restrict__ sums, const double* __restrict__ count, int G,
+                              double* __restrict__ emean, float* seeds) {
   long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (emean && w < G) emean[w] = count[w] > 0.0 ? sums[w] / count[w] : 0.0;
   if (w >= B) return;
   int g = geo ? geo[w] : 0;
-  seeds[w] = (float)(2.0 * ((double)eloc[w] - emean[g]) / count[g]);
+  const double m = sums[g] / count[g];
+  seeds[w] = (float)(2.0 * ((double)eloc[w] - m) / count[g]);
 }
 
 __global__ void k_d2f(const double* a, float* b, long n) {
@@ -267,9 +273,10 @@ void launch_esum(cudaStream_t s, const float* eloc, int G, const long* d_off, co
   if (G > 0) FN_COUNT(1), k_emean<<<G, 256, 0, s>>>(eloc, d_off, d_cnt, B1, 0, sums);
 }
 
-void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean,
-                        const double* count, float* seeds) {
-  if (B > 0) FN_COUNT(1), k_seeds_given<<<nblk(B, 256), 256, 0, s>>>(eloc, B, geo, emean, count, seeds);
+void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* sums,
+                        const double* count, int G, double* emean, float* seeds) {
+  const long n = std::max<long>(B, emean ? G : 0);
+  if (n > 0) FN_COUNT(1), k_seeds_given<<<nblk(n, 256), 256, 0, s>>>(eloc, B, geo, sums, count, G, emean, seeds);
 }
 
 void launch_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean, const long* d_cnt,

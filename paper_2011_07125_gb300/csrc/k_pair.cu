@@ -289,8 +289,8 @@ void launch_inst(cudaStream_t s, PairArgs a) {
   auto kern = k_pair_layer<DIN, DO, Q, LAYER>;
   constexpr int MB = min_blocks<Q, LAYER>();
   const size_t budget = kSmemPerSM / MB - 1024;
-  static std::once_flag once;
-  std::call_once(once, [&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget); });
+  static PerDeviceOnce attr;  // the attribute is per function and device
+  attr([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget); });
   // groups per tile: about one task (layer) or two output steps (means) per
   // thread, within the shared-memory share of the resident blocks
   const int per_group = LAYER ? (a.n * (DO / 8) + (Q == 1 ? 3 : 0)) / (Q == 1 ? 4 : 1) : a.C * (int)(a.ldm / 8);

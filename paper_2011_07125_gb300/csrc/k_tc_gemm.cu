@@ -26,6 +26,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <stdlib.h>
+
 #include <mutex>
 
 #include "fn_internal.cuh"
@@ -36,10 +38,14 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;            // 64 bf16 = 128 bytes: one swizzle row
-constexpr int STAGES = 4;  // at most; fewer when the residual region needs the space
+constexpr int STAGES = 4;      // default ring depth cap; fewer when the residual region needs the space
+constexpr int MAX_STAGES = 8;  // barrier slots reserved in shared memory
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int SMEM_BYTES = 227 * 1024;  // dynamic shared memory requested per CTA
 constexpr int BAR_BYTES = 256;
+// full and empty slots, two accumulator pairs, the residual pair, the TMEM
+// address and the abort flag
+static_assert((2 * MAX_STAGES + 4 + 2) * 8 + 8 <= BAR_BYTES, "barrier region too small");
 constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
@@ -198,8 +204,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
   uint8_t* resr = smem + nst * stage_bytes;                   // residual region (1024-aligned)
   const int res_half = 2 * a.tile_n * BK * 2;                 // two k-blocks of one part (hi or lo)
   uint64_t* full = reinterpret_cast<uint64_t*>(resr + (a.res_smem ? 2 * res_half : 0));
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
+  uint64_t* empty = full + MAX_STAGES;
+  uint64_t* tfull = empty + MAX_STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* rfull = tempty + 2;
   uint64_t* rempty = rfull + 1;
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < MAX_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -686,29 +692,19 @@ bool tc_make_map(CUtensorMap* tm, const void* base, long rows, long ld_elems, in
   return r == CUDA_SUCCESS;
 }
 
-int tc_num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
-}
-
 fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
+  static PerDeviceOnce attr;  // the attribute is per function and device
+  attr([] { cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES); });
   TcGemmArgs a = a0;
   // ring depth from the shared memory left after the residual region
   const int stage_bytes = A_BYTES + a.tile_n * BK * 2;
   const int res_bytes = a.res_smem ? 4 * a.tile_n * BK * 2 : 0;
   const int avail = SMEM_BYTES - 1024 - BAR_BYTES - res_bytes;
   a.stages = avail / stage_bytes;
-  if (a.stages > STAGES) a.stages = STAGES;
+  int cap = STAGES;
+  if (const char* v = getenv("FERMINET_TC_STAGES")) cap = atoi(v);
+  if (cap < 2 || cap > MAX_STAGES) cap = STAGES;
+  if (a.stages > cap) a.stages = cap;
   if (a.stages < 2) return FN_EINVAL;
   if (a.res_smem && (a.mode != 1 || a.tile_n % 8)) return FN_EINVAL;
   if (a.mode == 1 && (a.U || a.C < 8 || a.C % 8 || a.tile_n % a.C)) return FN_EINVAL;  // layer: no per-walker term
@@ -723,7 +719,7 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
   }
   const long total = (long)a.n_tiles_n * a.n_tiles_m;
   if (total <= 0) return FN_OK;
-  int grid = tc_num_sms();
+  int grid = device_sm_count();
   if (total < grid) grid = (int)total;
   FN_COUNT(1), k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(a);
   return FN_OK;

@@ -30,8 +30,9 @@ def reduce_energy_grad(local_sums, local_counts, partial_grad: Callable, group=N
     """Two-phase reduction of the VMC energy gradient.
 
     local_sums, local_counts: float64 tensors [G] (this process's energy sum
-    and walker count per geometry).  partial_grad(emean, count) returns this
-    process's float64 gradient share [P] for the batch-wide mean and count.
+    and walker count per geometry).  partial_grad(sums, counts), given the
+    batch-wide sums and counts, returns (emean [G], this process's float64
+    gradient share [P]); the division happens behind the C ABI.
     Returns (emean [G], grad [P]), float64 and identical on every process.
     """
     import torch
@@ -41,8 +42,8 @@ def reduce_energy_grad(local_sums, local_counts, partial_grad: Callable, group=N
     if _world(group) > 1:
         dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
     sums, counts = buf[:G].contiguous(), buf[G:].contiguous()
-    emean = torch.where(counts > 0, sums / counts.clamp_min(1.0), torch.zeros_like(sums))
-    grad = partial_grad(emean, counts).to(torch.float64)
+    emean, grad = partial_grad(sums, counts)
+    grad = grad.to(torch.float64)
     if _world(group) > 1:
         dist.all_reduce(grad, op=dist.ReduceOp.SUM, group=group)
     return emean, grad
@@ -54,4 +55,4 @@ def energy_grad(fn, x, eloc, group=None):
     (fn: a binding.FermiNet).  Returns (emean [G], grad [P]) as float64."""
     B = x.shape[0]
     return reduce_energy_grad(fn.energy_sums(eloc), fn.walker_counts(B),
-                              lambda em, cnt: fn.energy_grad_partial(x, eloc, em, cnt), group)
+                              lambda sums, cnt: fn.energy_grad_partial(x, eloc, sums, cnt), group)

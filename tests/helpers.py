@@ -64,3 +64,16 @@ def logpsi_bound(net, ref, u=U32, base=TOL_LOGPSI_REL):
 def emean_bound(net, ref, u=U32, base=TOL_EMEAN_ABS):
     S, _ = conditioning(ref)
     return base + gamma(net) * u * S.mean()
+
+
+# Mixed path (BF16 hi + lo operands, about 16 significant bits: u = 2^-17).
+U_MIXED = 2.0 ** -17
+TOL_EMEAN_MIXED = 1e-3
+TOL_GRAD_MIXED = 1e-2
+TOL_ELOC_ABS_MIXED = 1e-3
+
+
+def mixed_eloc_bound(net, ref):
+    """Per-walker E_L bound of the mixed path: the rounding model above with
+    the mixed unit roundoff."""
+    return eloc_bound(net, ref, u=U_MIXED, base=TOL_ELOC_ABS_MIXED)

@@ -36,3 +36,29 @@ def test_gemm_class_bytes_match_launch_count(name):
 def test_gemm_class_bytes_c4h6_value():
     # 30 electrons, 92 real columns, 10 nuclei, d1 = 256, d2 = 32, 16 determinants
     assert bench.gemm_class_alg_bytes(synth.workload("c4h6").net) == 29257472
+
+
+def _bench(*args, env=None):
+    import subprocess
+    e = dict(os.environ)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        e.pop(k, None)
+    e.update(env or {})
+    return subprocess.run([sys.executable, bench.__file__, *args], capture_output=True, text=True, env=e,
+                          timeout=300)
+
+
+def test_gpus_flag_starts_that_many_ranks():
+    """`bench.py --gpus 2` without a launcher starts two ranks itself (host
+    ranks over gloo here), and rank 0 reports both."""
+    import json
+    r = _bench("--gpus", "2", "--check-launch")
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["n_gpus"] == 2 and line["ranks"] == [0, 1]
+
+
+def test_gpus_flag_disagreeing_with_launcher_fails():
+    r = _bench("--gpus", "2", "--check-launch", env={"WORLD_SIZE": "1", "RANK": "0"})
+    assert r.returncode != 0
+    assert "--gpus 2" in r.stderr

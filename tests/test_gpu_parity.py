@@ -242,8 +242,10 @@ def test_two_replicas_add_to_whole_batch(name, per):
         fns.append((f, cuda(x[idx]), cuda(eloc[idx])))
     sums = sum(f.energy_sums(e) for f, _, e in fns)
     cnts = sum(f.walker_counts(xr.shape[0]) for f, xr, _ in fns)
-    emean = sums / cnts
-    grad = sum(f.energy_grad_partial(xr, e, emean, cnts) for f, xr, e in fns)
+    parts = [f.energy_grad_partial(xr, e, sums, cnts) for f, xr, e in fns]
+    emean = parts[0][0]
+    assert torch.equal(emean, parts[1][0])
+    grad = sum(g for _, g in parts)
     em_o, g_o = oracle.energy_grad(wl.net, P, wl.geoms, x, eloc, geo=geo)
     np.testing.assert_allclose(emean.cpu().numpy(), em_o, rtol=1e-12, atol=1e-12)
     err = np.linalg.norm(grad.cpu().numpy() - g_o) / np.linalg.norm(g_o)

@@ -5,6 +5,7 @@ index, transposed operand, wrong factor) that would otherwise go unnoticed.
 None of them compares the oracle with itself through the same code path.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -332,6 +333,18 @@ def test_mcmc_normals_are_standard_normal():
     # Philox is a bijection for a fixed key: distinct counters, distinct blocks
     seen = {tuple(oracle.philox4x32_10([i, 0, 0, 0], [1, 2])) for i in range(2000)}
     assert len(seen) == 2000
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the published known-answer vectors
+    (tests/golden/philox4x32_10_kat.txt): a swapped output word, a wrong round
+    or Weyl constant, or a missing round changes every vector."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        assert oracle.philox4x32_10(v[0:4], v[4:6]) == v[6:10]
 
 
 def test_mcmc_hydrogen_samples_psi_squared():

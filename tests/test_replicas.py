@@ -49,10 +49,11 @@ def _local(net, geoms, P, x, geo, eloc, G):
     sums = torch.tensor([eloc[geo == g].sum() for g in range(G)], dtype=torch.float64)
     cnts = torch.tensor([float((geo == g).sum()) for g in range(G)], dtype=torch.float64)
 
-    def partial(em, cnt):
-        em, cnt = em.numpy(), cnt.numpy()
+    def partial(esum, cnt):
+        esum, cnt = esum.numpy(), cnt.numpy()
+        em = esum / cnt
         seeds = 2.0 * (eloc - em[geo]) / cnt[geo]
-        return torch.from_numpy(oracle.logpsi_vjp(net, P, geoms, x, seeds, geo=geo))
+        return torch.from_numpy(em), torch.from_numpy(oracle.logpsi_vjp(net, P, geoms, x, seeds, geo=geo))
 
     return sums, cnts, partial
 
@@ -73,7 +74,7 @@ def _worker(rank, world, port, q):
         em, grad = replicas.reduce_energy_grad(sums, cnts, partial)
         # the same shares with each rank's own mean energy (no first exchange)
         em_l = sums / cnts
-        g_l = partial(em_l, cnts * world).clone()
+        g_l = partial(em_l * cnts * world, cnts * world)[1].clone()
         dist.all_reduce(g_l)
         q.put((rank, em.numpy(), grad.numpy(), g_l.numpy(), None))
         dist.destroy_process_group()

@@ -69,3 +69,36 @@ def test_noalloc_rejects_network_beyond_scratch():
                                      out.data_ptr(), None, None)
     torch.cuda.synchronize()
     assert binding.STATUS[rc] == "FN_ENOMEM"
+
+
+def test_noalloc_back_to_back_on_side_stream():
+    """Two calls queued back to back on one non-default stream, with no
+    synchronisation between them: the second call's clearing of the status
+    header and its reuse of the array are ordered after the first call's
+    kernels by the stream, so both results equal ferminet_logpsi's."""
+    lib, binding = _lib()
+    wl, lay, P, x, geo = setup("ne", 40)
+    fn = binding.FermiNet(wl.net, wl.geoms, counts=wl.counts, precision="fp32")
+    params = torch.from_numpy(P).cuda()
+    fn.set_params(params)
+    R = torch.from_numpy(np.asarray(wl.geoms[0].R, np.float32).reshape(-1, 3)).cuda()
+    net = binding._net(wl.net)
+    x2 = x.copy()
+    x2[:, :, 1] -= 0.2
+    xs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (x, x2)]
+    refs = [fn.logpsi(xx) for xx in xs]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    outs = []
+    with torch.cuda.stream(side):
+        for xx in xs:
+            lp = torch.full((len(x),), float("nan"), device="cuda")
+            sg = torch.zeros(len(x), device="cuda")
+            rc = lib.ferminet_logpsi_noalloc(C.byref(net), params.data_ptr(), R.data_ptr(), xx.data_ptr(), len(x),
+                                             lp.data_ptr(), sg.data_ptr(), C.c_void_p(side.cuda_stream))
+            assert rc == 0
+            outs.append((lp, sg))
+    side.synchronize()
+    for (lp, sg), (ref, ref_sign) in zip(outs, refs):
+        assert torch.equal(sg, ref_sign)
+        assert rel_err(lp.cpu().numpy(), ref.cpu().numpy()).max() <= TOL_LOGPSI_REL
