@@ -189,6 +189,35 @@ fn_status ferminet_energy_grad_partial(fn_ctx* ctx, const float* d_x, long B, co
                                        const double* d_esum, const double* d_count, double* d_emean,
                                        double* d_grad64);
 
+/* Options of the training loop around the hot path.  The paper states
+ * neither; both follow the practice of the FermiNet training it builds on
+ * (Sec. 2 raises the Metropolis moves between updates from 10 to 20, Table 2
+ * runs 50).
+ *   clip_scale > 0: the VMC gradient (ferminet_energy_grad, ferminet_step)
+ *     uses clipped local energies.  Per geometry g: m_g = median of E_L (the
+ *     mean of the two middle values for an even count), tv_g = mean of
+ *     |E_L - m_g|, c_w = E_L,w clamped to [m_g - clip_scale tv_g,
+ *     m_g + clip_scale tv_g], and walker w gets the weight
+ *     2 (c_w - mean_g c) / B_g.  d_emean still receives the plain mean of E_L.
+ *     Medians, spreads and means are formed in FP64 on the device.  0 = off
+ *     (the default).  The replica form (ferminet_energy_grad_partial) refuses
+ *     clipping (FN_EINVAL): a median is not a sum over processes.
+ *   d_width (device float, or NULL = off): the Metropolis moves of
+ *     ferminet_mcmc_step and ferminet_step read the proposal width from
+ *     *d_width (their width argument is ignored), and after the moves of each
+ *     call the library updates it from that call's acceptance fraction
+ *     p = accepted / (B n_steps): *d_width *= width_factor if p > accept_hi,
+ *     /= width_factor if p < accept_lo (in FP64, stored as float).  The
+ *     buffer is caller-owned and must outlive its use; a captured step keeps
+ *     reading it on every replay.
+ * Changing the options re-captures the graph of ferminet_step. */
+typedef struct {
+  float clip_scale;
+  float* d_width;
+  float accept_lo, accept_hi, width_factor;
+} fn_train_opts;
+fn_status ferminet_set_train_opts(fn_ctx* ctx, const fn_train_opts* opts);
+
 /* n_steps Gaussian all-electron Metropolis moves sampling |psi|^2 (Eq. 2).
  * Step s uses counter t = counter + s.  For walker w the proposal is
  * x' = x + width * z with z drawn by Philox4x32-10 (key {seed lo, seed hi},

@@ -87,6 +87,11 @@ def _load():
     lib.oracle_mcmc.argtypes = [np_, dp, dp, dp, ip, C.c_long, dp, dp, C.c_int, C.c_double,
                                 C.c_ulonglong, C.c_ulonglong, ip, dp]
     lib.oracle_logpsi_jet.argtypes = [np_, dp, dp, dp, C.c_int, dp, dp]
+    lib.oracle_clip_seeds.argtypes = [C.c_int, C.c_long, ip, dp, C.c_double, dp, dp]
+    lib.oracle_energy_grad_clipped.argtypes = [np_, dp, dp, dp, ip, C.c_int, C.c_long, dp, dp, C.c_double, dp,
+                                               dp]
+    lib.oracle_adapt_width.argtypes = [C.c_double] * 6
+    lib.oracle_adapt_width.restype = C.c_double
     _lib = lib
     return lib
 
@@ -203,6 +208,47 @@ def energy_grad(net, params, geoms, x, eloc, geo=None):
     if rc:
         raise ValueError("oracle_energy_grad failed")
     return em, grad
+
+
+def clip_seeds(eloc, scale, geo=None, n_geo=None):
+    """(seeds [B], stats [G,3] = median, mean |E_L - median|, clipped mean) of
+    the clipped VMC gradient."""
+    lib = _load()
+    e = _d(eloc)
+    B = e.shape[0]
+    g = _geo_idx(geo, B)
+    G = int(n_geo if n_geo is not None else (int(g[:B].max()) + 1 if B else 1))
+    seeds = np.zeros(max(B, 1))
+    stats = np.zeros((G, 3))
+    rc = lib.oracle_clip_seeds(G, B, g.ctypes.data_as(C.POINTER(C.c_int)), _dp(e) if B else None, float(scale),
+                               _dp(seeds), _dp(stats))
+    if rc:
+        raise ValueError("oracle_clip_seeds failed")
+    return seeds[:B], stats
+
+
+def energy_grad_clipped(net, params, geoms, x, eloc, scale, geo=None):
+    """(emean [G], grad [P]) of the VMC gradient with clipped local energies."""
+    lib = _load()
+    x = _d(x)
+    B = x.shape[0]
+    R, Z = _geo_arrays(geoms, net.n_nuc)
+    P = _d(params)
+    e = _d(eloc)
+    grad = np.zeros(P.shape[0])
+    em = np.zeros(len(geoms))
+    g = _geo_idx(geo, B)
+    rc = lib.oracle_energy_grad_clipped(C.byref(_net(net)), _dp(P), _dp(R), _dp(Z),
+                                        g.ctypes.data_as(C.POINTER(C.c_int)), len(geoms), B, _dp(x), _dp(e),
+                                        float(scale), _dp(em), _dp(grad))
+    if rc:
+        raise ValueError("oracle_energy_grad_clipped failed")
+    return em, grad
+
+
+def adapt_width(width, accepted, moves, lo, hi, factor):
+    return _load().oracle_adapt_width(float(width), float(accepted), float(moves), float(lo), float(hi),
+                                      float(factor))
 
 
 def mcmc(net, params, geoms, x, logpsi0, n_steps, width, seed, counter, geo=None):

@@ -828,6 +828,78 @@ int oracle_energy_grad(const onet* t, const double* P, const double* R, const do
 }
 
 /* ------------------------------------------------------------------------ */
+/* Training-loop pieces around the gradient (FermiNet practice; the paper    */
+/* is silent on both): local-energy clipping and proposal-width adaptation   */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+/* Clipped gradient seeds.  For every geometry g (walkers W_g): the median m_g
+ * of E_L over W_g (the mean of the two middle values when |W_g| is even),
+ * the spread tv_g = mean over W_g of |E_L - m_g|, the clipped energies
+ * c_w = min(max(E_L,w, m_g - scale tv_g), m_g + scale tv_g), their mean
+ * cbar_g, and seeds[w] = 2 (c_w - cbar_g) / |W_g|.  stats (may be NULL)
+ * receives {m_g, tv_g, cbar_g} per geometry. */
+int oracle_clip_seeds(int n_geo, long B, const int* geo, const double* eloc, double scale, double* seeds,
+                      double* stats) {
+  if (n_geo < 1 || scale < 0) return -1;
+  double* buf = malloc(sizeof(double) * (B > 0 ? B : 1));
+  for (int g = 0; g < n_geo; ++g) {
+    long c = 0;
+    for (long w = 0; w < B; ++w)
+      if ((geo ? geo[w] : 0) == g) buf[c++] = eloc[w];
+    double m = 0.0, tv = 0.0, cbar = 0.0;
+    if (c > 0) {
+      qsort(buf, (size_t)c, sizeof(double), cmp_double);
+      m = (c % 2) ? buf[c / 2] : 0.5 * (buf[c / 2 - 1] + buf[c / 2]);
+      for (long i = 0; i < c; ++i) tv += fabs(buf[i] - m);
+      tv /= (double)c;
+      const double lo = m - scale * tv, hi = m + scale * tv;
+      for (long w = 0; w < B; ++w)
+        if ((geo ? geo[w] : 0) == g) cbar += fmin(fmax(eloc[w], lo), hi);
+      cbar /= (double)c;
+      for (long w = 0; w < B; ++w)
+        if ((geo ? geo[w] : 0) == g) seeds[w] = 2.0 * (fmin(fmax(eloc[w], lo), hi) - cbar) / (double)c;
+    }
+    if (stats) { stats[3 * g] = m; stats[3 * g + 1] = tv; stats[3 * g + 2] = cbar; }
+  }
+  free(buf);
+  return 0;
+}
+
+/* VMC energy gradient with clipped local energies: emean[g] is the plain
+ * mean of E_L over geometry g (the energy estimate), and grad =
+ * sum_w seeds[w] d log|psi_w| / d theta with the seeds of oracle_clip_seeds. */
+int oracle_energy_grad_clipped(const onet* t, const double* P, const double* R, const double* Z, const int* geo,
+                               int n_geo, long B, const double* x, const double* eloc, double scale, double* emean,
+                               double* grad) {
+  if (check_net(t) || n_geo < 1) return -1;
+  double* sum = calloc(n_geo, sizeof(double));
+  long* cnt = calloc(n_geo, sizeof(long));
+  for (long w = 0; w < B; ++w) { sum[GEO(w)] += eloc[w]; cnt[GEO(w)]++; }
+  for (int g = 0; g < n_geo; ++g) emean[g] = cnt[g] ? sum[g] / cnt[g] : 0.0;
+  double* seeds = malloc(sizeof(double) * (B > 0 ? B : 1));
+  int rc = oracle_clip_seeds(n_geo, B, geo, eloc, scale, seeds, NULL);
+  if (!rc) rc = oracle_logpsi_vjp(t, P, R, Z, geo, B, x, seeds, grad);
+  free(seeds); free(sum); free(cnt);
+  return rc;
+}
+
+/* Proposal-width adaptation from the acceptance fraction of the last moves:
+ * p = accepted / moves; the width grows by `factor` when p > hi, shrinks by
+ * it when p < lo, and stays otherwise. */
+double oracle_adapt_width(double width, double accepted, double moves, double lo, double hi, double factor) {
+  if (moves <= 0) return width;
+  const double p = accepted / moves;
+  if (p > hi) return width * factor;
+  if (p < lo) return width / factor;
+  return width;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Philox4x32-10 and Metropolis                                              */
 /* ------------------------------------------------------------------------ */
 

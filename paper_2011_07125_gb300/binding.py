@@ -40,6 +40,11 @@ class FnTuning(C.Structure):
                 ("residual_smem", C.c_int), ("pair_unfused", C.c_int)]
 
 
+class FnTrainOpts(C.Structure):
+    _fields_ = [("clip_scale", C.c_float), ("d_width", C.c_void_p), ("accept_lo", C.c_float),
+                ("accept_hi", C.c_float), ("width_factor", C.c_float)]
+
+
 class FnParamEntry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("offset", C.c_long), ("count", C.c_long),
                 ("fan_in", C.c_long), ("kind", C.c_int), ("pad", C.c_int)]
@@ -62,7 +67,7 @@ EXPORTS = ("ferminet_init", "ferminet_param_layout", "ferminet_net_layout", "fer
            "ferminet_logpsi", "ferminet_local_energy", "ferminet_logpsi_vjp", "ferminet_energy_grad",
            "ferminet_energy_sums", "ferminet_energy_grad_partial", "ferminet_mcmc_step", "ferminet_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
            "ferminet_profile_read", "ferminet_launch_count", "ferminet_get_tuning", "ferminet_set_tuning",
-           "ferminet_autotune", "ferminet_last_error", "ferminet_destroy")
+           "ferminet_autotune", "ferminet_set_train_opts", "ferminet_last_error", "ferminet_destroy")
 KERNEL_CLASSES = {"tangent_gemm": 0, "det_tangent": 1, "two_layer": 2, "means": 3, "tanh": 4, "value_pass": 5,
                   "adjoint": 6}
 
@@ -109,6 +114,7 @@ def load(path: Optional[str] = None):
         lib.ferminet_get_tuning.argtypes = [vp, C.POINTER(FnTuning)]
         lib.ferminet_set_tuning.argtypes = [vp, C.POINTER(FnTuning)]
         lib.ferminet_autotune.argtypes = [vp, vp, C.c_long, C.c_int, C.POINTER(FnTuning)]
+        lib.ferminet_set_train_opts.argtypes = [vp, C.POINTER(FnTrainOpts)]
         lib.ferminet_launch_count.argtypes = []
         lib.ferminet_launch_count.restype = C.c_longlong
         for f in EXPORTS:
@@ -362,6 +368,18 @@ class FermiNet:
         except OSError:
             pass
         return best, False
+
+    def set_train_opts(self, clip_scale=0.0, width=None, accept_lo=0.5, accept_hi=0.55, width_factor=1.1):
+        """Training-loop options: local-energy clipping in the gradient
+        (clip_scale > 0) and proposal-width adaptation (width: a float32 CUDA
+        tensor of one element that the moves read and the library updates;
+        None = off)."""
+        if width is not None:
+            self._f32(width, (1,))
+        self._width_ref = width
+        o = FnTrainOpts(float(clip_scale), None if width is None else width.data_ptr(), float(accept_lo),
+                        float(accept_hi), float(width_factor))
+        self._check(self.lib.ferminet_set_train_opts(self.ctx, C.byref(o)), "ferminet_set_train_opts")
 
     def flagged_matrices(self):
         return int(self.lib.ferminet_flagged_matrices(self.ctx))

@@ -979,28 +979,54 @@ fn_status value_pass_fixed_workspace(const fn_net& net, const float* d_params, c
 
 namespace {
 
-// The whole VMC step: n_steps Metropolis moves (counter = base + s, with the
-// base either `counter` or, when dctr is set, read from device memory), then
-// the local energy at the new positions, then the VMC energy gradient.
-fn_status run_step(fn_ctx* c, float* x, float* lp, long B, int n_steps, float width, uint64_t seed,
-                   uint64_t counter, const uint64_t* dctr, float* eloc, double* emean, float* grad, int* acc) {
+// Metropolis moves over the batch (counter = base + s, the base either
+// `counter` or, when dctr is set, read from device memory); with the training
+// option d_width the width comes from device memory and is adapted from the
+// acceptance of these moves afterwards.
+fn_status run_moves(fn_ctx* c, float* x, float* lp, long B, int n_steps, float width, uint64_t seed,
+                    uint64_t counter, const uint64_t* dctr, int* acc) {
   const int n3 = 3 * c->n;
   float* xp = c->aux;
   float* lpp = c->aux + (size_t)B * n3;
-  float* seeds = c->aux;  // reused after the moves
+  float* dw = c->train.d_width;
+  if (dw && !acc) acc = reinterpret_cast<int*>(c->aux + (size_t)B * (n3 + 1));  // counts for the adaptation
   if (acc) cudaMemsetAsync(acc, 0, sizeof(int) * B, c->stream);
   for (int s = 0; s < n_steps; ++s) {
     const uint64_t t = (dctr ? 0 : counter) + (uint64_t)s;
-    launch_propose(c->stream, x, xp, B, n3, width, seed, t, dctr);
+    launch_propose(c->stream, x, xp, B, n3, width, seed, t, dctr, dw);
     fn_status st = run_passes(c, xp, B, false, FwdOut{lpp, nullptr, nullptr, nullptr});
     if (st != FN_OK) return st;
     launch_accept(c->stream, x, xp, lp, lpp, B, n3, seed, t, acc, dctr);
   }
-  fn_status st = run_passes(c, x, B, true, FwdOut{nullptr, nullptr, eloc, nullptr});
-  if (st != FN_OK) return st;
+  if (dw && n_steps > 0)
+    launch_adapt_width(c->stream, acc, B, n_steps, dw, c->train.accept_lo, c->train.accept_hi,
+                       c->train.width_factor);
+  return FN_OK;
+}
+
+// Per-geometry mean energies into emean and the gradient seeds (clipped when
+// the training option asks for it).
+void energy_seeds(fn_ctx* c, const float* eloc, long B, double* emean, float* seeds) {
   const long B1 = c->G > 1 ? -1 : B;
+  const int* geo = c->G > 1 ? c->d_geo : nullptr;
   launch_emean(c->stream, eloc, c->G, c->d_geo_off, c->d_geo_cnt, B1, emean);
-  launch_seeds(c->stream, eloc, B, c->G > 1 ? c->d_geo : nullptr, emean, c->d_geo_cnt, B1, seeds);
+  if (c->train.clip_scale > 0.f)
+    launch_clip_seeds(c->stream, eloc, B, geo, c->G, c->d_geo_off, c->d_geo_cnt, B1, (double)c->train.clip_scale,
+                      c->d_clip_stats, seeds);
+  else
+    launch_seeds(c->stream, eloc, B, geo, emean, c->d_geo_cnt, B1, seeds);
+}
+
+// The whole VMC step: n_steps Metropolis moves, then the local energy at the
+// new positions, then the VMC energy gradient.
+fn_status run_step(fn_ctx* c, float* x, float* lp, long B, int n_steps, float width, uint64_t seed,
+                   uint64_t counter, const uint64_t* dctr, float* eloc, double* emean, float* grad, int* acc) {
+  float* seeds = c->aux;  // reused after the moves
+  fn_status st = run_moves(c, x, lp, B, n_steps, width, seed, counter, dctr, acc);
+  if (st != FN_OK) return st;
+  st = run_passes(c, x, B, true, FwdOut{nullptr, nullptr, eloc, nullptr});
+  if (st != FN_OK) return st;
+  energy_seeds(c, eloc, B, emean, seeds);
   return run_vjp(c, x, B, seeds, grad);
 }
 
@@ -1102,6 +1128,7 @@ fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms
   if (bad(cudaMalloc(&c->d_geo, sizeof(int) * geo.size()))) return FN_ENOMEM;
   if (bad(cudaMalloc(&c->d_geo_off, sizeof(long) * n_geoms))) return FN_ENOMEM;
   if (bad(cudaMalloc(&c->d_geo_cnt, sizeof(long) * n_geoms))) return FN_ENOMEM;
+  if (bad(cudaMalloc(&c->d_clip_stats, sizeof(double) * 3 * n_geoms))) return FN_ENOMEM;
   if (bad(cudaMalloc(&c->d_status, sizeof(unsigned)))) return FN_ENOMEM;
   if (bad(cudaMalloc(&c->d_flagged, sizeof(unsigned long long)))) return FN_ENOMEM;
   if (bad(cudaMemset(c->d_params, 0, sizeof(float) * std::max<long>(c->lay.total, 1)))) return FN_ECUDA;
@@ -1232,9 +1259,7 @@ fn_status ferminet_energy_grad(fn_ctx* c, const float* d_x, long B, const float*
   st = ensure_aux(c, std::max<long>(B, 1));
   if (st != FN_OK) return st;
   float* seeds = c->aux;
-  const long B1 = c->G > 1 ? -1 : B;
-  launch_emean(c->stream, d_eloc, c->G, c->d_geo_off, c->d_geo_cnt, B1, d_emean);
-  launch_seeds(c->stream, d_eloc, B, c->G > 1 ? c->d_geo : nullptr, d_emean, c->d_geo_cnt, B1, seeds);
+  energy_seeds(c, d_eloc, B, d_emean, seeds);
   return run_vjp(c, d_x, B, seeds, d_grad);
 }
 
@@ -1256,6 +1281,8 @@ fn_status ferminet_energy_grad_partial(fn_ctx* c, const float* d_x, long B, cons
   if (st != FN_OK) return st;
   if (!d_grad64 || !d_esum || !d_count || (!d_eloc && B > 0))
     return fail(c, FN_EINVAL, "null eloc, energy sum, count or grad pointer");
+  if (c->train.clip_scale > 0.f)
+    return fail(c, FN_EINVAL, "the replica form does not clip: a median is not a sum over processes");
   st = ensure_aux(c, std::max<long>(B, 1));
   if (st != FN_OK) return st;
   float* seeds = c->aux;
@@ -1273,18 +1300,23 @@ fn_status ferminet_mcmc_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int
   if (B == 0) return FN_OK;
   st = ensure_aux(c, B);
   if (st != FN_OK) return st;
-  const int n3 = 3 * c->n;
-  float* xp = c->aux;
-  float* lpp = c->aux + (size_t)B * n3;
-  if (d_accepted) CK(cudaMemsetAsync(d_accepted, 0, sizeof(int) * B, c->stream));
-  for (int s = 0; s < n_steps; ++s) {
-    const uint64_t tc = counter + (uint64_t)s;
-    launch_propose(c->stream, d_x, xp, B, n3, width, seed, tc, nullptr);
-    st = run_passes(c, xp, B, false, FwdOut{lpp, nullptr, nullptr, nullptr});
-    if (st != FN_OK) return st;
-    launch_accept(c->stream, d_x, xp, d_logpsi, lpp, B, n3, seed, tc, d_accepted, nullptr);
-  }
+  st = run_moves(c, d_x, d_logpsi, B, n_steps, width, seed, counter, nullptr, d_accepted);
+  if (st != FN_OK) return st;
   return after_launch(c);
+}
+
+fn_status ferminet_set_train_opts(fn_ctx* c, const fn_train_opts* o) {
+  if (!c || !o) return FN_EINVAL;
+  if (!(o->clip_scale >= 0.f)) return fail(c, FN_EINVAL, "clip_scale must be >= 0");
+  if (o->d_width && !(o->width_factor >= 1.f && o->accept_lo >= 0.f && o->accept_lo <= o->accept_hi &&
+                      o->accept_hi <= 1.f))
+    return fail(c, FN_EINVAL, "width adaptation needs 0 <= accept_lo <= accept_hi <= 1 and width_factor >= 1");
+  c->train = *o;
+  if (c->step_exec) {  // a captured step holds the old options
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  return FN_OK;
 }
 
 fn_status ferminet_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_steps, float width, uint64_t seed,
@@ -1328,6 +1360,8 @@ fn_status ferminet_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_st
   key.ws = c->ws;
   key.aux = c->aux;
   key.ws_size = c->ws_size;
+  key.dwidth = c->train.d_width;
+  key.clip = c->train.clip_scale;
   const bool same = c->step_exec && memcmp(&key, &c->step_key, sizeof key) == 0;
   launch_set_u64(gs, c->d_counter, counter);
   if (!same) {
@@ -1507,6 +1541,7 @@ void ferminet_destroy(fn_ctx* c) {
   cudaFree(c->d_geo);
   cudaFree(c->d_geo_off);
   cudaFree(c->d_geo_cnt);
+  cudaFree(c->d_clip_stats);
   cudaFree(c->d_status);
   cudaFree(c->d_flagged);
   cudaFree(c->ws);

@@ -206,9 +206,10 @@ void launch_det_value_warp(cudaStream_t s, const DetArgs& a);  // k_det_value.cu
 void launch_combine(cudaStream_t s, const float* logdet, const float* sign, const float* dgrad, const float* dlap,
                     const float* x, long Bc, long w0, int n, int K, int N, Geo g, bool tangent, float* logpsi,
                     float* psign, float* eloc, float* kinetic, float* wdet, unsigned* status);
-// Metropolis kernels; with dctr non-null the counter is t + *dctr (device memory).
+// Metropolis kernels; with dctr non-null the counter is t + *dctr (device
+// memory); with dwidth non-null the proposal width is *dwidth.
 void launch_propose(cudaStream_t s, const float* x, float* xp, long B, int n3, float width, uint64_t seed,
-                    uint64_t t, const uint64_t* dctr);
+                    uint64_t t, const uint64_t* dctr, const float* dwidth);
 void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, const float* lp_prop, long B, int n3,
                    uint64_t seed, uint64_t t, int* accepted, const uint64_t* dctr);
 void launch_set_u64(cudaStream_t s, uint64_t* p, uint64_t v);
@@ -226,6 +227,13 @@ void launch_esum(cudaStream_t s, const float* eloc, int G, const long* d_off, co
                  double* sums);
 void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* geo, const double* sums,
                         const double* count, int G, double* emean, float* seeds);
+// Clipped gradient seeds (per geometry: median, mean absolute deviation and
+// clipped mean in FP64 into stats [3 G], then the seeds).
+void launch_clip_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, int G, const long* d_off,
+                       const long* d_cnt, long B1, double scale, double* stats, float* seeds);
+// *width adapted from the acceptance fraction sum(accepted) / (B n_steps).
+void launch_adapt_width(cudaStream_t s, const int* accepted, long B, int n_steps, float* width, double lo,
+                        double hi, double factor);
 void launch_d2f(cudaStream_t s, const double* a, float* b, long n);
 void launch_fill(cudaStream_t s, float* p, float v, long n);
 void launch_zero_d(cudaStream_t s, double* p, long n);
@@ -302,6 +310,8 @@ struct fn_ctx {
   __nv_bfloat16* ident = nullptr;  // 128 x 128 BF16 identity (operand of the folded per-walker term)
   int force64 = 0;
   fn_tuning tune{};  // 0 fields: defaults
+  fn_train_opts train{};       // clipping and width adaptation (off)
+  double* d_clip_stats = nullptr;  // [3 G]: median, spread, clipped mean per geometry
   // captured full step (ferminet_step with use_graph)
   uint64_t* d_counter = nullptr;
   cudaGraphExec_t step_exec = nullptr;
@@ -312,7 +322,8 @@ struct fn_ctx {
     int n_steps;
     float width;
     uint64_t seed;
-    const void *x, *lp, *eloc, *emean, *grad, *acc, *ws, *aux;
+    const void *x, *lp, *eloc, *emean, *grad, *acc, *ws, *aux, *dwidth;
+    float clip;
     size_t ws_size;
   } step_key{};
   // per-class event timing

@@ -145,8 +145,10 @@ __device__ __forceinline__ void box_muller(unsigned a, unsigned b, float& z0, fl
 }
 
 __global__ void k_propose(const float* __restrict__ x, float* __restrict__ xp, long B, int n3, float width,
-                          uint64_t seed, uint64_t t, const uint64_t* __restrict__ dctr) {
+                          uint64_t seed, uint64_t t, const uint64_t* __restrict__ dctr,
+                          const float* __restrict__ dwidth) {
   if (dctr) t += *dctr;  // graph replays read the step's base counter from device memory
+  if (dwidth) width = *dwidth;  // adaptive width, kept in device memory
   const int nb = (n3 + 3) / 4;
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= B * nb) return;
@@ -222,6 +224,120 @@ __global__ void k_seeds_given(const float* __restrict__ eloc, long B, const int*
   seeds[w] = (float)(2.0 * ((double)eloc[w] - m) / count[g]);
 }
 
+// Orderable unsigned key of a float (a < b  <=>  key(a) < key(b) for non-NaN).
+__device__ __forceinline__ unsigned fkey(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+constexpr int kClipThreads = 512;
+
+// Block sum of one double per thread (thread 0 gets the total).
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = kClipThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Clipping statistics of one geometry per block: the two middle order
+// statistics by a radix select over the orderable keys (four 8-bit passes,
+// both ranks at once), the median m, tv = mean |E_L - m| and the mean of the
+// clipped energies, all in FP64: stats[3 g + {0, 1, 2}].
+__global__ void __launch_bounds__(kClipThreads) k_clip_stats(const float* __restrict__ eloc,
+                                                             const long* __restrict__ off,
+                                                             const long* __restrict__ cnt, long B1, double scale,
+                                                             double* __restrict__ stats) {
+  __shared__ unsigned hist[2][256];
+  __shared__ unsigned pre[2], rank[2];
+  __shared__ double sh[kClipThreads];
+  const int g = blockIdx.x;
+  const long o = B1 >= 0 ? 0 : off[g], c = B1 >= 0 ? B1 : cnt[g];
+  if (c <= 0) {
+    if (threadIdx.x == 0) stats[3 * g] = stats[3 * g + 1] = stats[3 * g + 2] = 0.0;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    pre[0] = pre[1] = 0u;
+    rank[0] = (unsigned)((c - 1) / 2);
+    rank[1] = (unsigned)(c / 2);
+  }
+  unsigned mask = 0u;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 512; i += kClipThreads) (&hist[0][0])[i] = 0u;
+    __syncthreads();
+    const unsigned p0 = pre[0], p1 = pre[1];
+    for (long i = threadIdx.x; i < c; i += kClipThreads) {
+      const unsigned k = fkey(eloc[o + i]);
+      const unsigned b = (k >> shift) & 255u;
+      if ((k & mask) == p0) atomicAdd(&hist[0][b], 1u);
+      if ((k & mask) == p1) atomicAdd(&hist[1][b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      const int s = threadIdx.x;
+      unsigned r = rank[s], b = 0;
+      while (b < 255u && hist[s][b] <= r) {  // the rank lies in a later bucket
+        r -= hist[s][b];
+        ++b;
+      }
+      rank[s] = r;
+      pre[s] |= b << shift;
+    }
+    mask |= 255u << shift;
+    __syncthreads();
+  }
+  const double m = 0.5 * ((double)fkey_inv(pre[0]) + (double)fkey_inv(pre[1]));
+  double a = 0.0;
+  for (long i = threadIdx.x; i < c; i += kClipThreads) a += fabs((double)eloc[o + i] - m);
+  const double tv = block_sum(a, sh) / (double)c;
+  const double lo = m - scale * tv, hi = m + scale * tv;
+  double cs = 0.0;
+  for (long i = threadIdx.x; i < c; i += kClipThreads) cs += fmin(fmax((double)eloc[o + i], lo), hi);
+  const double cbar = block_sum(cs, sh) / (double)c;
+  if (threadIdx.x == 0) {
+    stats[3 * g] = m;
+    stats[3 * g + 1] = tv;
+    stats[3 * g + 2] = cbar;
+  }
+}
+
+__global__ void k_seeds_clip(const float* __restrict__ eloc, long B, const int* __restrict__ geo,
+                             const double* __restrict__ stats, const long* __restrict__ cnt, long B1, double scale,
+                             float* seeds) {
+  long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= B) return;
+  const int g = geo ? geo[w] : 0;
+  const double c = B1 >= 0 ? (double)B1 : (double)cnt[g];
+  const double m = stats[3 * g], tv = stats[3 * g + 1], cbar = stats[3 * g + 2];
+  const double e = fmin(fmax((double)eloc[w], m - scale * tv), m + scale * tv);
+  seeds[w] = (float)(2.0 * (e - cbar) / c);
+}
+
+// Proposal-width adaptation from the acceptance counts of the last moves.
+__global__ void __launch_bounds__(kClipThreads) k_adapt_width(const int* __restrict__ accepted, long B,
+                                                              int n_steps, float* width, double lo, double hi,
+                                                              double factor) {
+  __shared__ double sh[kClipThreads];
+  double a = 0.0;
+  for (long i = threadIdx.x; i < B; i += kClipThreads) a += (double)accepted[i];
+  const double tot = block_sum(a, sh);
+  if (threadIdx.x == 0 && B > 0 && n_steps > 0) {
+    const double p = tot / ((double)B * (double)n_steps);
+    const double w = (double)*width;
+    if (p > hi) *width = (float)(w * factor);
+    else if (p < lo) *width = (float)(w / factor);
+  }
+}
+
 __global__ void k_d2f(const double* a, float* b, long n) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -248,9 +364,9 @@ void launch_combine(cudaStream_t s, const float* logdet, const float* sign, cons
 }
 
 void launch_propose(cudaStream_t s, const float* x, float* xp, long B, int n3, float width, uint64_t seed,
-                    uint64_t t, const uint64_t* dctr) {
+                    uint64_t t, const uint64_t* dctr, const float* dwidth) {
   long tot = B * ((n3 + 3) / 4);
-  if (tot > 0) FN_COUNT(1), k_propose<<<nblk(tot, 256), 256, 0, s>>>(x, xp, B, n3, width, seed, t, dctr);
+  if (tot > 0) FN_COUNT(1), k_propose<<<nblk(tot, 256), 256, 0, s>>>(x, xp, B, n3, width, seed, t, dctr, dwidth);
 }
 
 void launch_accept(cudaStream_t s, float* x, const float* xp, float* logpsi, const float* lp_prop, long B, int n3,
@@ -282,6 +398,17 @@ void launch_seeds_given(cudaStream_t s, const float* eloc, long B, const int* ge
 void launch_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, const double* emean, const long* d_cnt,
                   long B1, float* seeds) {
   if (B > 0) FN_COUNT(1), k_seeds<<<nblk(B, 256), 256, 0, s>>>(eloc, B, geo, emean, d_cnt, B1, seeds);
+}
+
+void launch_clip_seeds(cudaStream_t s, const float* eloc, long B, const int* geo, int G, const long* d_off,
+                       const long* d_cnt, long B1, double scale, double* stats, float* seeds) {
+  if (G > 0) FN_COUNT(1), k_clip_stats<<<G, kClipThreads, 0, s>>>(eloc, d_off, d_cnt, B1, scale, stats);
+  if (B > 0) FN_COUNT(1), k_seeds_clip<<<nblk(B, 256), 256, 0, s>>>(eloc, B, geo, stats, d_cnt, B1, scale, seeds);
+}
+
+void launch_adapt_width(cudaStream_t s, const int* accepted, long B, int n_steps, float* width, double lo,
+                        double hi, double factor) {
+  FN_COUNT(1), k_adapt_width<<<1, kClipThreads, 0, s>>>(accepted, B, n_steps, width, lo, hi, factor);
 }
 
 void launch_d2f(cudaStream_t s, const double* a, float* b, long n) {

@@ -365,3 +365,67 @@ def test_mcmc_hydrogen_samples_psi_squared():
     r = float(np.mean(rs))
     assert abs(r - 1.5) < 0.05, r
     np.testing.assert_allclose(lp, -np.linalg.norm(x[:, 0], axis=1), atol=1e-12)
+
+
+def test_clip_seeds_reduce_to_plain_estimator_and_vanish_at_zero_width():
+    """Clipping (the training-loop option around the gradient): with a band
+    wide enough to clip nothing, the clipped gradient is the plain VMC
+    gradient of oracle_energy_grad; with a zero-width band every energy is
+    clipped to the median and the gradient vanishes."""
+    net = synth.Net(2, 8, 4, 2, 2, 1, 1)
+    lay, P = _params(net, 7)
+    x = np.random.default_rng(21).standard_normal((9, 3, 3))
+    eloc = np.random.default_rng(22).standard_normal(9) * 3 - 7
+    em, g = oracle.energy_grad(net, P, [synth.atom(3)], x, eloc)
+    em_c, g_c = oracle.energy_grad_clipped(net, P, [synth.atom(3)], x, eloc, 1e9)
+    np.testing.assert_allclose(em_c, em, rtol=1e-15)
+    np.testing.assert_allclose(g_c, g, rtol=1e-9, atol=1e-12 * np.abs(g).max())
+    em0, g0 = oracle.energy_grad_clipped(net, P, [synth.atom(3)], x, eloc, 0.0)
+    np.testing.assert_allclose(em0, em, rtol=1e-15)
+    assert np.abs(g0).max() == 0.0
+
+
+@pytest.mark.parametrize("B", [1, 2, 7, 10, 101])
+def test_clip_seeds_median_spread_band_and_centering(B):
+    rng = np.random.default_rng(23 + B)
+    e = rng.standard_normal(B) * 2 - 5
+    if B > 3:
+        e[1] = 400.0   # outliers on both sides
+        e[2] = -900.0
+    scale = 1.5
+    seeds, st = oracle.clip_seeds(e, scale)
+    m, tv, cbar = st[0]
+    # median and mean absolute deviation against the library routines
+    assert m == np.median(e)
+    np.testing.assert_allclose(tv, np.mean(np.abs(e - np.median(e))), rtol=1e-14)
+    # the clipped energy behind every seed lies in the band and equals E_L inside it
+    c = seeds * B / 2 + cbar
+    lo, hi = m - scale * tv, m + scale * tv
+    assert np.all(c >= lo - 1e-12) and np.all(c <= hi + 1e-12)
+    inside = (e > lo) & (e < hi)
+    np.testing.assert_allclose(c[inside], e[inside], rtol=1e-13, atol=1e-12)
+    if B > 3:
+        np.testing.assert_allclose(c[[1, 2]], [hi, lo], rtol=1e-13)
+    # centred seeds; invariant under a permutation of the walkers
+    assert abs(seeds.sum()) < 1e-12 * max(1.0, np.abs(seeds).max() * B)
+    perm = rng.permutation(B)
+    s2, _ = oracle.clip_seeds(e[perm], scale)
+    np.testing.assert_allclose(s2, seeds[perm], rtol=1e-14, atol=1e-15)
+
+
+def test_clip_seeds_geometries_are_independent():
+    rng = np.random.default_rng(31)
+    e = rng.standard_normal(12)
+    geo = np.array([0, 1, 0, 1, 1, 0, 0, 1, 0, 0, 1, 1], np.int32)
+    seeds, st = oracle.clip_seeds(e, 2.0, geo=geo, n_geo=2)
+    for g in range(2):
+        sg, stg = oracle.clip_seeds(e[geo == g], 2.0)
+        np.testing.assert_allclose(seeds[geo == g], sg, rtol=1e-15)
+        np.testing.assert_allclose(st[g], stg[0], rtol=1e-15)
+
+
+def test_adapt_width_cases():
+    assert oracle.adapt_width(0.02, 60, 100, 0.5, 0.55, 1.1) == pytest.approx(0.022, rel=1e-15)
+    assert oracle.adapt_width(0.02, 40, 100, 0.5, 0.55, 1.1) == pytest.approx(0.02 / 1.1, rel=1e-15)
+    assert oracle.adapt_width(0.02, 52, 100, 0.5, 0.55, 1.1) == 0.02
+    assert oracle.adapt_width(0.02, 0, 0, 0.5, 0.55, 1.1) == 0.02
