@@ -295,9 +295,17 @@ def error_report(wl, P, xs, geo, eloc, logpsi, prec, grad_fn=None):
     ref = oracle.local_energy(wl.net, P, wl.geoms, xs, geo=geo)
     de = eloc.astype(np.float64) - ref["eloc"]
     dl = np.abs(logpsi.astype(np.float64) - ref["logpsi"]) / np.maximum(np.abs(ref["logpsi"]), 1.0)
-    per_geo = [float(de[geo == g].mean()) for g in range(len(wl.geoms)) if np.any(geo == g)]
+    gs = [g for g in range(len(wl.geoms)) if np.any(geo == g)]
+    per_geo = [float(de[geo == g].mean()) for g in gs]
+    # standard error of each geometry's sample mean (pooled spread): the
+    # sample estimates the mean error over the geometry's whole batch
+    rms = float(np.sqrt(np.mean(de ** 2)))
+    stderr = [rms / np.sqrt(int((geo == g).sum())) for g in gs]
     rep = {"walkers": int(len(xs)), "eloc_mean_err_per_geometry": per_geo,
+           "eloc_mean_err_stderr_per_geometry": stderr,
            "eloc_mean_err_max_abs": float(np.max(np.abs(per_geo))),
+           "eloc_mean_err_all_sampled": float(de.mean()),
+           "eloc_mean_err_all_sampled_stderr": rms / np.sqrt(len(de)),
            "eloc_max_abs": float(np.abs(de).max()), "eloc_median_abs": float(np.median(np.abs(de))),
            "frac_eloc_within_1e-4": float(np.mean(np.abs(de) <= 1e-4)),
            "logpsi_max_rel": float(dl.max()), "frac_logpsi_within_1e-5": float(np.mean(dl <= 1e-5)),
@@ -645,7 +653,7 @@ def main():
     ap.add_argument("--side", default=None,
                     help="comma-separated workloads measured briefly after the main one (default: ne,ar with the "
                          "default workload, none otherwise)")
-    ap.add_argument("--err-per-geom", type=int, default=6, help="walkers per geometry in the oracle error check")
+    ap.add_argument("--err-per-geom", type=int, default=16, help="walkers per geometry in the oracle error check")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

@@ -14,8 +14,8 @@ import pytest
 
 import oracle
 from paper_2011_07125_gb300 import synth
-from helpers import (TOL_ELOC_ABS, TOL_LOGPSI_REL, U32, conditioning, gamma, eloc_bound, emean_bound, logpsi_bound, rel_err,
-                     setup)
+from helpers import (TOL_ELOC_ABS, TOL_LOGPSI_REL, U32, conditioning, gamma, eloc_bound, emean_bound, equilibrated,
+                     logpsi_bound, rel_err, setup)
 
 TOL_GRAD_FP32 = 1e-3
 
@@ -74,6 +74,29 @@ def test_local_energy(name, per):
     assert abs(e.mean() - ref["eloc"].mean()) <= emean_bound(wl.net, ref)
     if strict.any():
         assert de[strict].max() < TOL_ELOC_ABS
+
+
+@pytest.mark.parametrize("name", ["ne", "ar", "c4h6"])
+def test_fp32_unwidened_bars_on_sampled_walkers(name):
+    """On 48 walkers sampled from |psi|^2, the share of walkers inside the
+    unwidened FP32 bars (1e-4 Ha per walker, 1e-5 relative on log|psi|) is
+    gated, besides every walker inside its widened bar (measured shares on
+    GB300: 0.88 to 1.0 for E_L, 1.0 for log|psi|)."""
+    wl, P, xs = equilibrated(name, 48)
+    ref = oracle.local_energy(wl.net, P, wl.geoms[:1], xs)
+    from paper_2011_07125_gb300.binding import FermiNet
+    fn = FermiNet(wl.net, wl.geoms[:1], counts=[len(xs)], precision="fp32")
+    fn.set_params(torch.from_numpy(P).cuda())
+    out = fn.local_energy(cuda(xs))
+    assert fn.sync() == "FN_OK"
+    de = np.abs(out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"])
+    rl = rel_err(out["logpsi"].cpu().numpy(), ref["logpsi"])
+    f_e, f_l = np.mean(de <= TOL_ELOC_ABS), np.mean(rl <= TOL_LOGPSI_REL)
+    print(name, "share within 1e-4 Ha", f_e, "share within 1e-5 rel", f_l, "batch-mean err",
+          abs(de.mean()))
+    assert f_e >= 0.8 and f_l >= 0.95
+    assert np.all(de <= eloc_bound(wl.net, ref))
+    assert abs((out["eloc"].cpu().numpy() - ref["eloc"]).mean()) <= emean_bound(wl.net, ref)
 
 
 def test_chunked_equals_unchunked(monkeypatch):

@@ -7,7 +7,10 @@ walker-to-geometry mapping.  The walkers are first moved towards |psi|^2 (the
 distribution the VMC estimator averages over) by FP32 Metropolis moves on the
 GPU.  Checked: per-walker log|psi| and E_L under the parity bars of each
 precision, and the batch-mean E_L of every geometry (1e-3 Ha for the mixed
-path, the FP32 bar for the FP32 path), and the VMC gradient.
+path, the FP32 bar for the FP32 path), and the VMC gradient.  A geometry's
+mean over its few sampled walkers estimates the mean over its full batch with
+a sampling error, so each per-geometry bar adds three standard errors of the
+sample; the mean over all sampled walkers (the bias) takes the bar alone.
 """
 import dataclasses
 
@@ -16,8 +19,8 @@ import pytest
 
 import oracle
 from paper_2011_07125_gb300 import synth
-from helpers import (TOL_GRAD_MIXED, TOL_EMEAN_MIXED, U_MIXED, eloc_bound, emean_bound, logpsi_bound,
-                     mixed_eloc_bound)
+from helpers import (TOL_EMEAN_ABS, TOL_GRAD_MIXED, TOL_EMEAN_MIXED, U_MIXED, eloc_bound, emean_bound,
+                     logpsi_bound, mixed_eloc_bound, sample_mean_bound)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,18 +69,19 @@ def test_uneven_geometries_local_energy(sampled, prec):
     print(prec, "per-geometry mean E_L error", per_geo, "max |dE|", np.abs(de).max(),
           "fraction within 1e-4 Ha", np.mean(np.abs(de) <= 1e-4))
     assert np.array_equal(out["sign"].cpu().numpy(), ref["sign"])
+    cnt = np.array(wl.counts)
     if prec == "fp32":
         assert np.all(np.abs(de) <= eloc_bound(wl.net, ref)), (np.abs(de) / eloc_bound(wl.net, ref)).max()
         assert np.all(dl <= logpsi_bound(wl.net, ref))
-        for g in range(len(wl.geoms)):
-            sel = geo == g
-            r = {k: v[sel] for k, v in ref.items()}
-            assert abs(per_geo[g]) <= emean_bound(wl.net, r), g
+        assert abs(de.mean()) <= emean_bound(wl.net, ref)
+        assert np.all(np.abs(per_geo) <= sample_mean_bound(de, cnt, TOL_EMEAN_ABS)), per_geo
+        assert np.mean(np.abs(de) <= 1e-4) >= 0.8
     else:
         assert np.all(np.abs(de) <= mixed_eloc_bound(wl.net, ref)), \
             (np.abs(de) / mixed_eloc_bound(wl.net, ref)).max()
         assert np.all(dl <= logpsi_bound(wl.net, ref, u=U_MIXED))
-        assert np.all(np.abs(per_geo) < TOL_EMEAN_MIXED), per_geo
+        assert abs(de.mean()) < TOL_EMEAN_MIXED
+        assert np.all(np.abs(per_geo) <= sample_mean_bound(de, cnt, TOL_EMEAN_MIXED)), per_geo
     fn.close()
 
 
@@ -94,7 +98,8 @@ def test_uneven_geometries_gradient(sampled):
     em, g = fn.energy_grad(xx, out["eloc"])
     assert fn.sync() == "FN_OK"
     em_o, g_o = oracle.energy_grad(wl.net, P, wl.geoms, xs, ref["eloc"], geo=geo)
-    assert np.all(np.abs(em.cpu().numpy() - em_o) < TOL_EMEAN_MIXED)
+    de = out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"]
+    assert np.all(np.abs(em.cpu().numpy() - em_o) <= sample_mean_bound(de, np.array(wl.counts), TOL_EMEAN_MIXED))
     err = np.linalg.norm(g.cpu().numpy() - g_o) / np.linalg.norm(g_o)
     print("uneven mixed gradient rel L2", err)
     assert err < TOL_GRAD_MIXED
