@@ -261,13 +261,18 @@ fn_status ferminet_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_
  *                  two-electron stream run as separate kernels (the plain
  *                  schedule, kept for comparison and for shapes the fused
  *                  kernel does not cover); 0 = one fused pass (default).
- *                  Not varied by the autotuner. */
+ *                  Not varied by the autotuner;
+ *   adjoint_simt:  FN_PREC_MIXED only: 1 = the adjoint (its stored value
+ *                  pass and its contractions) runs on the FP32 SIMT GEMMs;
+ *                  0 = on the tensor cores with BF16 hi + lo operands and FP32
+ *                  accumulation (default).  Not varied by the autotuner. */
 typedef struct {
   int layer_groups;
   int feature_tile;
   long tangent_chunk;
   int residual_smem;
   int pair_unfused;
+  int adjoint_simt;
 } fn_tuning;
 
 fn_status ferminet_get_tuning(const fn_ctx* ctx, fn_tuning* out);

@@ -24,6 +24,15 @@ extern "C" {
 fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, float* d_C, int M, int N, int K, int tile_n,
                                   int rows_on_lanes, void* stream, unsigned* d_status);
 
+/* The same GEMM split over K, as the weight-gradient contractions of the
+ * tensor-core adjoint run it (A rows on the lanes): the K/64 k-blocks are cut
+ * into ksplit ranges of ceil(K/64 / ksplit) (every range non-empty, else
+ * FN_EINVAL) and range z stores
+ *   d_C[z][n][m] = sum_{k in range z} A[m][k] * B[n][k]
+ * (d_C: [ksplit][N][M] float32). */
+fn_status ferminet_diag_bf16_gemm_splitk(const void* d_A, const void* d_B, float* d_C, int M, int N, int K,
+                                         int tile_n, int ksplit, void* stream, unsigned* d_status);
+
 #ifdef __cplusplus
 }
 #endif

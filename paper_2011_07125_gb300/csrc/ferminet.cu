@@ -95,6 +95,12 @@ struct FwdOut {
 
 // Value-pass activations kept for the adjoint.
 struct Stored {
+  // tensor-core store (mixed precision): activations and spin means as BF16
+  // hi + lo, tanh values as FP32; otherwise everything FP32
+  bool tc = false;
+  __nv_bfloat16* Hb[17][2] = {};
+  __nv_bfloat16* M1b[16][2] = {};
+  __nv_bfloat16* M2b[16][2] = {};
   float* H[17] = {};
   float* Y[16] = {};
   float* E[17] = {};
@@ -228,6 +234,13 @@ bool tc_segment(TcGemmArgs& g, int seg, const __nv_bfloat16* w_hi, const __nv_bf
   return ok;
 }
 
+// Whether the value pass that the adjoint stores runs on the tensor cores
+// (mixed precision; the stored tanh values come from the rows-on-lanes layer
+// epilogue, which needs d1 % 8 == 0).
+bool tc_store_ok(const fn_ctx* c) {
+  return c->prec == FN_PREC_MIXED && c->tc_ok && c->net.d1 % 8 == 0 && c->tune.adjoint_simt == 0;
+}
+
 // One network pass (see the file comment) over walkers [w0, w0 + Bc).
 void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangent, bool store, const FwdOut& out,
              Stored* st) {
@@ -242,7 +255,25 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   float* H0 = ar.get<float>(rows * 4 * N);
   float* E0 = ar.get<float>(pairs * Q * 4);
   float *Ha = nullptr, *Hb = nullptr, *Ea = nullptr, *Eb = nullptr, *M1 = nullptr, *M2 = nullptr;
-  if (store) {
+  const bool tc = c->prec == FN_PREC_MIXED && c->tc_ok && layer_tile(C) > 0 && (!store || tc_store_ok(c));
+  const bool two = c->terms > 1;
+  if (store && tc) {
+    st->tc = true;
+    st->E[0] = E0;
+    for (int l = 0; l < L; ++l) {
+      st->Y[l] = ar.get<float>(Bc * n * d1);
+      if (l < L - 1) {
+        st->E[l + 1] = ar.get<float>(pairs * Q * d2);
+        st->Y2[l] = ar.get<float>(pairs * d2);
+      }
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        st->Hb[l + 1][h] = ar.get<__nv_bfloat16>(rows * pad64(d1));
+        st->M1b[l][h] = ar.get<__nv_bfloat16>(Bc * C * pad64(2 * din1_of(t, l)));
+        st->M2b[l][h] = ar.get<__nv_bfloat16>(rows * pad64(2 * din2_of(t, l)));
+      }
+    }
+    M1 = ar.get<float>(Bc * C * 2 * max_din1);  // layer 0's means before their split
+  } else if (store) {
     st->H[0] = H0;
     st->E[0] = E0;
     for (int l = 0; l < L; ++l) {
@@ -268,8 +299,6 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     M2 = ar.get<float>(rows * 2 * max_din2);
   }
   float* U = ar.get<float>(Bc * C * d1);
-  const bool tc = !store && c->prec == FN_PREC_MIXED && c->tc_ok && layer_tile(C) > 0;
-  const bool two = c->terms > 1;
   float* Z = tc ? nullptr : ar.get<float>(rows * d1);
   __nv_bfloat16 *H0b[2] = {}, *Hab[2] = {}, *Hbb[2] = {}, *M1b[2] = {}, *M2b[2] = {};
   const long ldh0 = pad64(4 * N), ldh = pad64(d1), ldm1 = pad64(2 * max_din1), ldm2 = pad64(2 * max_din2);
@@ -279,10 +308,16 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   if (tc) {
     for (int h = 0; h < (two ? 2 : 1); ++h) {
       H0b[h] = ar.get<__nv_bfloat16>(rows * ldh0);
-      Hab[h] = ar.get<__nv_bfloat16>(rows * ldh);
-      Hbb[h] = ar.get<__nv_bfloat16>(rows * ldh);
-      M1b[h] = ar.get<__nv_bfloat16>(Bc * C * ldm1);
-      M2b[h] = ar.get<__nv_bfloat16>(rows * ldm2);
+      if (!store) {
+        Hab[h] = ar.get<__nv_bfloat16>(rows * ldh);
+        Hbb[h] = ar.get<__nv_bfloat16>(rows * ldh);
+        M1b[h] = ar.get<__nv_bfloat16>(Bc * C * ldm1);
+        M2b[h] = ar.get<__nv_bfloat16>(rows * ldm2);
+      }
+    }
+    if (store) {
+      st->Hb[0][0] = H0b[0];
+      st->Hb[0][1] = H0b[1];
     }
   }
   float* O = ar.get<float>(rows * Ktot);
@@ -355,14 +390,21 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     const int tl = tangent ? layer_tile(C, c->tune.layer_groups) : plain_tile(rows);
     if (ldh != d1) {  // padding columns must read as zeros in the MMAs
       for (int h = 0; h < (two ? 2 : 1); ++h) {
-        cudaMemsetAsync(Hab[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
-        cudaMemsetAsync(Hbb[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
+        if (Hab[h]) cudaMemsetAsync(Hab[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
+        if (Hbb[h]) cudaMemsetAsync(Hbb[h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
         if (Ub[h]) cudaMemsetAsync(Ub[h], 0, sizeof(__nv_bfloat16) * Bc * C * ldh, s);
+        for (int l = 1; store && l <= L; ++l)
+          cudaMemsetAsync(st->Hb[l][h], 0, sizeof(__nv_bfloat16) * rows * ldh, s);
       }
     }
     for (int l = 0; l < L; ++l) {
       const int a1 = din1_of(t, l), a2 = din2_of(t, l);
       const long l1 = pad64(2 * a1), l2 = pad64(2 * a2);
+      if (store)  // this layer's stored spin means (the fused pair kernel of layer l - 1 wrote M2b)
+        for (int h = 0; h < 2; ++h) {
+          M1b[h] = st->M1b[l][h];
+          M2b[h] = st->M2b[l][h];
+        }
       {
         Prof pm(c, tangent ? FN_KC_MEANS : FN_KC_COUNT, 0.0);
         if (l == 0) {
@@ -402,7 +444,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         u.status = c->d_status;
         if (!ok || tc_gemm_launch(s, u) != FN_OK) c->host_fail = true;
       }
-      __nv_bfloat16** Hnb = (l % 2 == 0) ? Hab : Hbb;
+      __nv_bfloat16** Hnb = store ? st->Hb[l + 1] : ((l % 2 == 0) ? Hab : Hbb);
       {
         Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, fl_rows * n * d1 * (double)(a1 + 2 * a2));
         TcGemmArgs m{};
@@ -464,16 +506,22 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
         m.hb_hi = Hnb[0];
         m.hb_lo = two ? Hnb[1] : nullptr;
         m.ldhb = ldh;
+        if (store) {  // tanh values for the adjoint
+          m.y_out = st->Y[l];
+          m.ldy = d1;
+        }
         m.status = c->d_status;
         if (!ok || tc_gemm_launch(s, m) != FN_OK) c->host_fail = true;
       }
       if (l < L - 1) {
-        float* En = (l % 2 == 0) ? Ea : Eb;
+        float* En = store ? st->E[l + 1] : ((l % 2 == 0) ? Ea : Eb);
+        float* Y2 = store ? st->Y2[l] : nullptr;
+        __nv_bfloat16** M2n = store ? st->M2b[l + 1] : M2b;
         Prof p2(c, FN_KC_TWO_LAYER, 2.0 * (double)pairs * Q * d2 * a2);
         if (fused)  // after this layer's GEMMs have read M2b: it now receives layer l + 1's means
-          pair_layer(l, Ec, l + 1 < L - 1 ? En : nullptr, nullptr, nullptr, M2b[0], M2b[1]);
+          pair_layer(l, Ec, (store || l + 1 < L - 1) ? En : nullptr, Y2, nullptr, M2n[0], two ? M2n[1] : nullptr);
         else
-          launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En, nullptr);
+          launch_two_layer(s, Ec, Bc, n, Q, a2, d2, P + c->lay.W[l], P + c->lay.c[l], l >= 1, En, Y2);
         Ec = En;
       }
       Hcb[0] = Hnb[0];
@@ -618,8 +666,257 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
                  out.kinetic, store ? st->wdet : nullptr, c->d_status);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core contractions of the adjoint (BF16 hi + lo operands, FP32
+// accumulation in TMEM).
+
+// Split count of a weight-gradient contraction: about two waves of tiles.
+int tn_ksplit(long Pn, long Qn, long K) {
+  int ntn = 1;
+  feature_tile(Pn, &ntn);
+  const long tiles = (long)ntn * ((Qn + 127) / 128);
+  const long kb = K / 64;
+  long want = (2L * device_sm_count() + tiles - 1) / tiles;
+  if (want > kb) want = kb;
+  if (want < 1) want = 1;
+  const long kps = (kb + want - 1) / want;
+  return (int)((kb + kps - 1) / kps);
+}
+
+// grad[p * ldg + q] += sum_k Bt[p][k] At[q][k] (k < K, a multiple of 64):
+// features-on-M GEMM split over k, FP32 partials reduced in FP64.
+bool tc_tn(fn_ctx* c, cudaStream_t s, long Pn, long Qn, long K, __nv_bfloat16* const at[2],
+           __nv_bfloat16* const bt[2], double* grad, long ldg, float* part) {
+  const bool two = c->terms > 1;
+  TcGemmArgs g{};
+  int ntn = 1;
+  const int tn = feature_tile(Pn, &ntn);
+  bool ok = tc_make_map(&g.A[0][0], at[0], Qn, K, 128) && tc_make_map(&g.B[0][0], bt[0], Pn, K, tn);
+  if (two)
+    ok = ok && tc_make_map(&g.A[0][1], at[1], Qn, K, 128) && tc_make_map(&g.B[0][1], bt[1], Pn, K, tn);
+  else {
+    g.A[0][1] = g.A[0][0];
+    g.B[0][1] = g.B[0][0];
+  }
+  if (!ok) return false;
+  g.kblocks[0] = (int)(K / 64);
+  g.nseg = 1;
+  g.terms = c->terms;
+  g.seg_terms[0] = c->terms;
+  g.rows = Pn;
+  g.mfeat = (int)Qn;
+  g.tile_n = tn;
+  g.n_tiles_n = ntn;
+  g.n_tiles_m = (int)((Qn + 127) / 128);
+  g.mode = 0;
+  g.out = part;
+  g.ldo = Qn;
+  g.bias_period = 1;
+  const int ks = tn_ksplit(Pn, Qn, K);
+  g.ksplit = ks;
+  g.kb_per_split = (int)((K / 64 + ks - 1) / ks);
+  g.split_stride = Pn * Qn;
+  g.status = c->d_status;
+  if (tc_gemm_launch(s, g) != FN_OK) return false;
+  launch_reduce_partials(s, part, ks, Pn, Qn, grad, ldg);
+  return true;
+}
+
+// out[r][j] = sum_k X[r][k] Wt[j][k] (j < Nn; k < K, a multiple of 64) in FP32:
+// rows-on-lanes GEMM.
+bool tc_nn(fn_ctx* c, cudaStream_t s, long rows, long Nn, long K, __nv_bfloat16* const xs[2],
+           const __nv_bfloat16* wt_hi, const __nv_bfloat16* wt_lo, float* out, long ldo) {
+  const bool two = c->terms > 1;
+  TcGemmArgs g{};
+  int ntf = 1;
+  const int tf = feature_tile(Nn, &ntf, c->tune.feature_tile);
+  if (!tc_segment_rm(g, 0, xs[0], two ? xs[1] : nullptr, rows, K, wt_hi, two ? wt_lo : nullptr, Nn, K, tf))
+    return false;
+  g.rm = 1;
+  g.nseg = 1;
+  g.terms = c->terms;
+  g.seg_terms[0] = c->terms;
+  g.rows = rows;
+  g.mfeat = (int)Nn;
+  g.tile_n = tf;
+  g.n_tiles_n = ntf;
+  g.n_tiles_m = (int)((rows + 127) / 128);
+  g.mode = 0;
+  g.out = out;
+  g.ldo = ldo;
+  g.bias_period = 1;
+  g.status = c->d_status;
+  return tc_gemm_launch(s, g) == FN_OK;
+}
+
+// Adjoint over one chunk on the tensor cores: the value pass is stored by the
+// tensor-core forward (activations and spin means as BF16 hi + lo, tanh values
+// FP32), and every contraction of the reverse pass -- weight gradients over
+// the rows (operands transposed so that the rows are contiguous, split over k
+// with an FP64 reduction) and backward-data products (transposed weights) --
+// runs on tcgen05.  Elementwise steps, the determinant adjoint and the
+// two-electron backward are those of the FP32 schedule.
+void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const float* seeds, double* grad) {
+  const fn_net& t = c->net;
+  const int n = c->n, N = c->N, L = t.n_layers, K = t.n_det, d1 = t.d1, d2 = t.d2;
+  const long Ktot = (long)K * n, rows = Bc * n, pairs = Bc * n * n;
+  const bool two = c->terms > 1;
+  Stored st;
+  float* lp = ar.get<float>(Bc);
+  forward(c, ar, x, Bc, w0, false, true, FwdOut{lp, nullptr, nullptr, nullptr}, &st);
+  const int max_din1 = std::max(4 * N, d1), max_din2 = std::max(4, d2);
+  const long ldk = pad64(rows), ldkw = pad64(Bc), lko = pad64(Ktot), ldh = pad64(d1), ldh0 = pad64(4 * N);
+  float* Obar = ar.get<float>(rows * Ktot);
+  float* envg = ar.get<float>(Bc * 2 * Ktot * N);
+  float* Hbar[2] = {ar.get<float>(rows * max_din1), ar.get<float>(rows * max_din1)};
+  float* Zbar = ar.get<float>(rows * d1);
+  float* Ebar[2] = {ar.get<float>(pairs * max_din2), ar.get<float>(pairs * max_din2)};
+  float* Z2bar = ar.get<float>(pairs * d2);
+  float* S = ar.get<float>(Bc * d1);
+  float* M1bar = ar.get<float>(Bc * 2 * max_din1);
+  float* M2bar = ar.get<float>(rows * 2 * max_din2);
+  long ta_rows = d1;
+  for (int l = 0; l < L; ++l)
+    ta_rows = std::max<long>({ta_rows, (long)din1_of(t, l), 2L * din2_of(t, l), 2L * din1_of(t, l)});
+  __nv_bfloat16 *Xs[2] = {}, *Ss[2] = {}, *TA[2] = {}, *TB[2] = {};
+  for (int h = 0; h < (two ? 2 : 1); ++h) {
+    Xs[h] = ar.get<__nv_bfloat16>(rows * std::max(lko, ldh));
+    Ss[h] = ar.get<__nv_bfloat16>(Bc * ldh);
+    TA[h] = ar.get<__nv_bfloat16>(ta_rows * ldk);
+    TB[h] = ar.get<__nv_bfloat16>(std::max<long>(Ktot, d1) * ldk);
+  }
+  long part_max = 0, cs_max = 0, tn_max = 0;
+  auto part_need = [&](long Pn, long Qn, long Kk) { part_max = std::max(part_max, tn_ksplit(Pn, Qn, Kk) * Pn * Qn); };
+  auto cs_need = [&](long r, long cl) { cs_max = std::max(cs_max, colsum_scratch_elems(r, cl)); };
+  part_need(Ktot, d1, ldk);
+  cs_need(Bc, 2 * Ktot * N);
+  cs_need(rows, Ktot);
+  for (int l = 0; l < L; ++l) {
+    const int a1 = din1_of(t, l), a2 = din2_of(t, l);
+    part_need(d1, a1, ldk);
+    part_need(d1, 2 * a2, ldk);
+    part_need(d1, 2 * a1, ldkw);
+    cs_need(rows, d1);
+    cs_need(pairs, d2);
+    tn_max = std::max(tn_max, (long)gemm_tn_splits(d2, a2, pairs) * d2 * a2);
+  }
+  float* part = ar.get<float>(part_max);
+  double* cs_scr = ar.get<double>(cs_max);
+  bool pair_bwd = c->tune.pair_unfused == 0;
+  for (int l = 0; l < L - 1 && pair_bwd; ++l) pair_bwd = pair_bwd_supported(din2_of(t, l), d2);
+  float* pb_scr = pair_bwd ? ar.get<float>(pair_bwd_scratch_floats(d2, d2)) : nullptr;
+  float* tn_scr = pair_bwd ? nullptr : ar.get<float>(tn_max);
+  if (ar.measure) return;
+
+  cudaStream_t s = c->stream;
+  const float* P = c->d_params;
+  const Layout& Lo = c->lay;
+  auto fail_if = [&](bool ok) {
+    if (!ok) c->host_fail = true;
+  };
+  cudaMemsetAsync(Obar, 0, sizeof(float) * rows * Ktot, s);
+  AdjDetArgs ad{};
+  ad.O = st.O;
+  ad.minv = st.minv;
+  ad.env = st.env;
+  ad.wdet = st.wdet;
+  ad.seeds = seeds;
+  ad.x = x;
+  ad.g = geo_of(c);
+  ad.w0 = w0;
+  ad.Bc = Bc;
+  ad.n = n;
+  ad.n_up = t.n_up;
+  ad.K = K;
+  ad.N = N;
+  ad.NS = c->ns_max;
+  ad.pi[0] = P + Lo.pi[0];
+  ad.pi[1] = P + Lo.pi[1];
+  ad.sigma[0] = P + Lo.sigma[0];
+  ad.sigma[1] = P + Lo.sigma[1];
+  ad.Obar = Obar;
+  ad.envgrad = envg;
+  launch_adj_det(s, ad);
+  launch_colsum_accum(s, envg, Bc, 2 * Ktot * N, 2 * Ktot * N, grad + Lo.pi[0], cs_scr);
+  // orbital weights: grad[q][f] += sum_r Obar[r][q] h^L[r][f]
+  launch_t_bf16(s, st.Hb[L][0], st.Hb[L][1], ldh, rows, d1, TA[0], TA[1], ldk);
+  launch_t_split(s, Obar, Ktot, rows, Ktot, TB[0], TB[1], ldk);
+  fail_if(tc_tn(c, s, Ktot, d1, ldk, TA, TB, grad + Lo.w_orb, d1, part));
+  launch_colsum_accum(s, Obar, rows, Ktot, Ktot, grad + Lo.g_orb, cs_scr);
+  // h^L gradient: Obar W_orb
+  launch_split_bf16(s, Obar, Ktot, rows, Ktot, Xs[0], Xs[1], lko);
+  fail_if(tc_nn(c, s, rows, d1, lko, Xs, c->wt_hi + c->wt_orb, c->wt_lo + c->wt_orb, Hbar[0], d1));
+  int hb = 0, eb = 0;
+  float* Enext = nullptr;
+  bool spread_pending = false;
+  for (int l = L - 1; l >= 0; --l) {
+    const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
+    float* Ecur = Ebar[eb];
+    if (l < L - 1 && pair_bwd) {
+      PairBwdArgs pb{};
+      pb.Eout_bar = Enext;
+      pb.M2bar = spread_pending ? M2bar : nullptr;
+      pb.n = n;
+      pb.n_up = t.n_up;
+      pb.Y = st.Y2[l];
+      pb.Ein = st.E[l];
+      pb.W = P + Lo.W[l];
+      pb.Ein_bar = l >= 1 ? Ecur : nullptr;
+      pb.residual = l >= 1 ? 1 : 0;
+      pb.pairs = pairs;
+      pb.grad_W = grad + Lo.W[l];
+      pb.grad_c = grad + Lo.c[l];
+      pb.partial = pb_scr;
+      fail_if(launch_pair_bwd(s, pb, a2, d2));
+    } else if (l < L - 1) {
+      launch_tanh_bwd(s, Enext, st.Y2[l], pairs, d2, Z2bar);
+      gemm_tn_accum(s, d2, a2, pairs, Z2bar, d2, st.E[l], a2, grad + Lo.W[l], a2, tn_scr,
+                    gemm_tn_splits(d2, a2, pairs));
+      launch_colsum_accum(s, Z2bar, pairs, d2, d2, grad + Lo.c[l], cs_scr);
+      gemm_nn(s, pairs, a2, d2, Z2bar, d2, P + Lo.W[l], a2, Ecur, a2, Epi{});
+      if (l >= 1) launch_add(s, Ecur, Enext, pairs * a2);
+    } else if (!pair_bwd) {
+      cudaMemsetAsync(Ecur, 0, sizeof(float) * pairs * a2, s);
+    }
+    float* Hcur = Hbar[hb];
+    launch_tanh_bwd(s, Hcur, st.Y[l], rows, d1, Zbar);
+    // V_a: grad[f][i] += sum_r Zbar[r][f] h^l[r][i]
+    launch_t_bf16(s, st.Hb[l][0], st.Hb[l][1], l == 0 ? ldh0 : ldh, rows, a1, TA[0], TA[1], ldk);
+    launch_t_split(s, Zbar, d1, rows, d1, TB[0], TB[1], ldk);
+    fail_if(tc_tn(c, s, d1, a1, ldk, TA, TB, grad + Lo.V[l], wV, part));
+    // V_de: the pair means
+    launch_t_bf16(s, st.M2b[l][0], st.M2b[l][1], pad64(2 * a2), rows, 2 * a2, TA[0], TA[1], ldk);
+    fail_if(tc_tn(c, s, d1, 2 * a2, ldk, TA, TB, grad + Lo.V[l] + 3 * a1, wV, part));
+    // V_bc: per-walker sums of Zbar against the one-electron means
+    launch_walker_sum(s, Zbar, Bc, n, d1, S);
+    launch_t_bf16(s, st.M1b[l][0], st.M1b[l][1], pad64(2 * a1), Bc, 2 * a1, TA[0], TA[1], ldkw);
+    launch_t_split(s, S, d1, Bc, d1, TB[0], TB[1], ldkw);
+    fail_if(tc_tn(c, s, d1, 2 * a1, ldkw, TA, TB, grad + Lo.V[l] + a1, wV, part));
+    launch_colsum_accum(s, Zbar, rows, d1, d1, grad + Lo.b[l], cs_scr);
+    if (l >= 1) {
+      float* Hprev = Hbar[hb ^ 1];
+      launch_split_bf16(s, Zbar, d1, rows, d1, Xs[0], Xs[1], ldh);
+      fail_if(tc_nn(c, s, rows, a1, ldh, Xs, c->wt_hi + c->wt_a[l], c->wt_lo + c->wt_a[l], Hprev, a1));
+      launch_add(s, Hprev, Hcur, rows * a1);
+      launch_split_bf16(s, S, d1, Bc, d1, Ss[0], Ss[1], ldh);
+      fail_if(tc_nn(c, s, Bc, 2 * a1, ldh, Ss, c->wt_hi + c->wt_bc[l], c->wt_lo + c->wt_bc[l], M1bar, 2 * a1));
+      launch_spread_mean1(s, M1bar, Bc, n, t.n_up, a1, Hprev);
+      fail_if(tc_nn(c, s, rows, 2 * a2, ldh, Xs, c->wt_hi + c->wt_de[l], c->wt_lo + c->wt_de[l], M2bar, 2 * a2));
+      if (pair_bwd) spread_pending = true;
+      else launch_spread_mean2(s, M2bar, Bc, n, t.n_up, a2, Ecur);
+      hb ^= 1;
+    }
+    Enext = (pair_bwd && l == L - 1) ? nullptr : Ecur;
+    eb ^= 1;
+  }
+}
+
 // Adjoint over one chunk: grad64 += sum_w seeds[w] d log|psi_w| / d theta.
 void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const float* seeds, double* grad) {
+  if (tc_store_ok(c)) {
+    vjp_chunk_tc(c, ar, x, Bc, w0, seeds, grad);
+    return;
+  }
   const fn_net& t = c->net;
   const int n = c->n, N = c->N, L = t.n_layers, K = t.n_det, d1 = t.d1, d2 = t.d2;
   const long Ktot = (long)K * n, rows = Bc * n, pairs = Bc * n * n;
@@ -1160,6 +1457,21 @@ fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms
     c->wb_orb = off;
     off += (long)t.n_det * c->n * c->ld_orb;
     c->wb_total = off;
+    long toff = 0;
+    const long ldt = pad64(t.d1);
+    for (int l = 0; l < t.n_layers; ++l) {
+      const int a1 = din1_of(t, l), a2 = din2_of(t, l);
+      c->wt_a[l] = toff;
+      toff += (long)a1 * ldt;
+      c->wt_bc[l] = toff;
+      toff += 2L * a1 * ldt;
+      c->wt_de[l] = toff;
+      toff += 2L * a2 * ldt;
+    }
+    c->wt_orb = toff;
+    toff += (long)t.d1 * pad64((long)t.n_det * c->n);
+    if (bad(cudaMalloc(&c->wt_hi, sizeof(__nv_bfloat16) * toff))) return FN_ENOMEM;
+    if (bad(cudaMalloc(&c->wt_lo, sizeof(__nv_bfloat16) * toff))) return FN_ENOMEM;
     if (bad(cudaMalloc(&c->wb_hi, sizeof(__nv_bfloat16) * off))) return FN_ENOMEM;
     if (bad(cudaMalloc(&c->wb_lo, sizeof(__nv_bfloat16) * off))) return FN_ENOMEM;
     if (bad(cudaMemset(c->wb_hi, 0, sizeof(__nv_bfloat16) * off))) return FN_ECUDA;
@@ -1219,6 +1531,17 @@ fn_status ferminet_set_params(fn_ctx* c, const float* d_params) {
     }
     launch_split_bf16(c->stream, P + c->lay.w_orb, t.d1, (long)t.n_det * c->n, t.d1, c->wb_hi + c->wb_orb,
                       c->wb_lo + c->wb_orb, c->ld_orb);
+    // transposed copies for the backward-data products of the adjoint
+    const long ldt = pad64(t.d1), Ktot = (long)t.n_det * c->n;
+    for (int l = 0; l < t.n_layers; ++l) {
+      const int a1 = din1_of(t, l), a2 = din2_of(t, l), wV = 3 * a1 + 2 * a2;
+      const float* V = P + c->lay.V[l];
+      launch_t_split(c->stream, V, wV, t.d1, a1, c->wt_hi + c->wt_a[l], c->wt_lo + c->wt_a[l], ldt);
+      launch_t_split(c->stream, V + a1, wV, t.d1, 2 * a1, c->wt_hi + c->wt_bc[l], c->wt_lo + c->wt_bc[l], ldt);
+      launch_t_split(c->stream, V + 3 * a1, wV, t.d1, 2 * a2, c->wt_hi + c->wt_de[l], c->wt_lo + c->wt_de[l], ldt);
+    }
+    launch_t_split(c->stream, P + c->lay.w_orb, t.d1, Ktot, t.d1, c->wt_hi + c->wt_orb, c->wt_lo + c->wt_orb,
+                   pad64(Ktot));
     CK(cudaGetLastError());
   }
   c->err.clear();
@@ -1408,7 +1731,8 @@ fn_status ferminet_get_tuning(const fn_ctx* c, fn_tuning* out) {
 fn_status ferminet_set_tuning(fn_ctx* c, const fn_tuning* t) {
   if (!c || !t) return FN_EINVAL;
   if (t->layer_groups < 0 || t->feature_tile < 0 || t->tangent_chunk < 0 || t->residual_smem < 0 ||
-      t->residual_smem > 1 || t->pair_unfused < 0 || t->pair_unfused > 1)
+      t->residual_smem > 1 || t->pair_unfused < 0 || t->pair_unfused > 1 || t->adjoint_simt < 0 ||
+      t->adjoint_simt > 1)
     return fail(c, FN_EINVAL, "bad tuning value");
   if (t->layer_groups > 0 && (t->layer_groups * c->Ct > 256 || (t->layer_groups * c->Ct) % 16))
     return fail(c, FN_EINVAL, "layer_groups gives an invalid tile");
@@ -1546,6 +1870,8 @@ void ferminet_destroy(fn_ctx* c) {
   cudaFree(c->d_flagged);
   cudaFree(c->ws);
   cudaFree(c->aux);
+  cudaFree(c->wt_hi);
+  cudaFree(c->wt_lo);
   cudaFree(c->wb_hi);
   cudaFree(c->wb_lo);
   cudaFree(c->ident);

@@ -101,6 +101,8 @@ void gemm_nn(cudaStream_t s, long M, long N, long K, const float* A, long lda, c
 void gemm_tn_accum(cudaStream_t s, long M, long N, long K, const float* A, long lda, const float* B, long ldb,
                    double* grad, long ldg, float* scratch, int splits);
 int gemm_tn_splits(long M, long N, long K);
+// grad[m * ldg + n] += sum_z part[z][m][n] in FP64 (z < splits, [M][N] each).
+void launch_reduce_partials(cudaStream_t s, const float* part, int splits, long M, long N, double* grad, long ldg);
 
 // ---------------------------------------------------------------------------
 // Network kernels (k_network.cu)
@@ -124,6 +126,13 @@ void launch_mean1_bf16(cudaStream_t s, const __nv_bfloat16* hi, const __nv_bfloa
 // dst_hi/lo[r][c] = split of src[r * src_ld + c] for c < cols, 0 for cols <= c < dst_ld.
 void launch_split_bf16(cudaStream_t s, const float* src, long src_ld, long rows, long cols, __nv_bfloat16* hi,
                        __nv_bfloat16* lo, long dst_ld);
+// Transposed splits (k_transpose.cu): dst_hi/lo[c][r] for c < cols and
+// r < ld_dst from src[r][c] (r < rows; zero for rows <= r < ld_dst), from FP32
+// or from BF16 hi + lo (lo parts may be null).
+void launch_t_split(cudaStream_t s, const float* src, long ld_src, long rows, long cols, __nv_bfloat16* hi,
+                    __nv_bfloat16* lo, long ld_dst);
+void launch_t_bf16(cudaStream_t s, const __nv_bfloat16* shi, const __nv_bfloat16* slo, long ld_src, long rows,
+                   long cols, __nv_bfloat16* hi, __nv_bfloat16* lo, long ld_dst);
 void launch_tanh_fl(cudaStream_t s, const float* Z, const float* Hres, long Bc, int n, int C, int d1, float* Hout,
                     float* Y);
 void launch_two_layer(cudaStream_t s, const float* Ein, long Bc, int n, int Q, int din2, int d2, const float* W,
@@ -307,6 +316,12 @@ struct fn_ctx {
   long wb_a[16] = {}, wb_bc[16] = {}, wb_de[16] = {}, wb_orb = 0;
   long ld_a[16] = {}, ld_bc[16] = {}, ld_de[16] = {}, ld_orb = 0;
   long wb_total = 0;
+  // transposed BF16 hi/lo weight blocks for the backward-data products of the
+  // tensor-core adjoint: V_a^T [a1][pad64(d1)], V_bc^T [2 a1][..], V_de^T
+  // [2 a2][..], W_orb^T [d1][pad64(K n)]
+  __nv_bfloat16* wt_hi = nullptr;
+  __nv_bfloat16* wt_lo = nullptr;
+  long wt_a[16] = {}, wt_bc[16] = {}, wt_de[16] = {}, wt_orb = 0;
   __nv_bfloat16* ident = nullptr;  // 128 x 128 BF16 identity (operand of the folded per-walker term)
   int force64 = 0;
   fn_tuning tune{};  // 0 fields: defaults

@@ -1,5 +1,5 @@
 // FP32 SIMT GEMM for the plain-FP32 path and the adjoint: 128x128 CTA tile,
-// 8-deep K slices double-buffered through shared memory, 8x8 outputs per
+// 16-deep K slices double-buffered through shared memory, 8x8 outputs per
 // thread.  Three operand orientations (NT forward, NN backward-data, TN
 // backward-weights with split-K and an FP64 reduction of the partials).
 #include "fn_internal.cuh"
@@ -196,6 +196,12 @@ void gemm_tn_accum(cudaStream_t s, long M, long N, long K, const float* A, long 
   run<false, false>(s, M, N, K, A, lda, B, ldb, scratch, N, e, kps, splits, 1);
   long tot = M * N;
   FN_COUNT(1), k_reduce_partials<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(scratch, splits, M, N, grad, ldg);
+}
+
+void launch_reduce_partials(cudaStream_t s, const float* part, int splits, long M, long N, double* grad, long ldg) {
+  const long tot = M * N;
+  if (tot > 0)
+    FN_COUNT(1), k_reduce_partials<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, splits, M, N, grad, ldg);
 }
 
 }  // namespace fn

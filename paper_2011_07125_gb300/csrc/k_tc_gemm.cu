@@ -166,15 +166,31 @@ __device__ __forceinline__ int res_blocks(const TcGemmArgs& a, int tm) {
   return nr < 0 ? 0 : (nr > 2 ? 2 : nr);
 }
 
-__device__ __forceinline__ int tile_items(const TcGemmArgs& a, int tm) {
+// first k-block and k-block count of split z (the whole range without a split)
+__device__ __forceinline__ int split_kb0(const TcGemmArgs& a, int z) { return a.ksplit > 1 ? z * a.kb_per_split : 0; }
+__device__ __forceinline__ int split_nkb(const TcGemmArgs& a, int z) {
+  if (a.ksplit <= 1) return a.kblocks[0];
+  const int r = a.kblocks[0] - z * a.kb_per_split;
+  return r < a.kb_per_split ? r : a.kb_per_split;
+}
+
+__device__ __forceinline__ int tile_items(const TcGemmArgs& a, int tm, int z) {
+  if (a.ksplit > 1) return split_nkb(a, z) * a.seg_terms[0];
   int n = 0;
   for (int sg = 0; sg < a.nseg; ++sg) n += a.kblocks[sg] * a.seg_terms[sg];
   return n;
 }
 
-__device__ __forceinline__ Item item_at(const TcGemmArgs& a, int tm, int nres, int i) {
+__device__ __forceinline__ Item item_at(const TcGemmArgs& a, int tm, int nres, int i, int z) {
   Item it;
   it.res = false;
+  if (a.ksplit > 1) {
+    const int nt = a.seg_terms[0];
+    it.sg = 0;
+    it.t = i % nt;
+    it.kb = split_kb0(a, z) + i / nt;
+    return it;
+  }
   for (int sg = 0; sg < a.nseg; ++sg) {
     const int nt = a.seg_terms[sg];
     const int cnt = a.kblocks[sg] * nt - (sg == 0 ? nres * nt : 0);
@@ -246,7 +262,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
   const uint32_t tmem_base = *tmem_slot;
 
   const int tile_n = a.tile_n;
-  const long total_tiles = (long)a.n_tiles_n * a.n_tiles_m;
+  const long mn_tiles = (long)a.n_tiles_n * a.n_tiles_m;
+  const long total_tiles = mn_tiles * (a.ksplit > 1 ? a.ksplit : 1);
   const uint32_t b_bytes = (uint32_t)tile_n * BK * 2;
 
   if (warp == 0) {
@@ -254,12 +271,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       int stage = 0;
       uint32_t phase = 0, rphase = 0;
       for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-        const int tn = (int)(tile / a.n_tiles_m), tm = (int)(tile % a.n_tiles_m);
+        const int z = (int)(tile / mn_tiles);
+        const long tmn = tile % mn_tiles;
+        const int tn = (int)(tmn / a.n_tiles_m), tm = (int)(tmn % a.n_tiles_m);
         const int nres = res_blocks(a, tm);
-        const int nit = tile_items(a, tm);
+        const int nit = tile_items(a, tm, z);
         bool ok = true;
         for (int i = 0; i < nit && ok; ++i) {
-          const Item it = item_at(a, tm, nres, i);
+          const Item it = item_at(a, tm, nres, i, z);
           if (it.res && it.kb == 2 * tm && it.t == 0) {
             // the residual region is free once the previous tile's epilogue is done
             if (!mbar_wait(rempty, rphase ^ 1, abort_flag, a.status)) {
@@ -318,16 +337,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       int acc = 0;
       uint32_t acc_phase = 0;
       for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-        const int tm = (int)(tile % a.n_tiles_m);
+        const int z = (int)(tile / mn_tiles);
+        const int tm = (int)((tile % mn_tiles) % a.n_tiles_m);
         const int nres = res_blocks(a, tm);
-        const int nit = tile_items(a, tm);
+        const int nit = tile_items(a, tm, z);
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, a.status)) break;
         fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
         bool ok = true;
         uint32_t first = 1;
         for (int i = 0; i < nit && ok; ++i) {
-          const Item it = item_at(a, tm, nres, i);
+          const Item it = item_at(a, tm, nres, i, z);
           if (it.res && it.kb == 2 * tm && it.t == 0) {
             if (!mbar_wait(rfull, rphase, abort_flag, a.status)) {
               ok = false;
@@ -379,12 +399,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     const __nv_bfloat16* __restrict__ rl = a.res_lo;
     __nv_bfloat16* __restrict__ oh = a.hb_hi;
     __nv_bfloat16* __restrict__ ol = a.hb_lo;
-    float* __restrict__ out = a.out;
     int acc = 0;
     uint32_t acc_phase = 0, rphase = 0;
     for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-      const int tn = (int)(tile / a.n_tiles_m), tm = (int)(tile % a.n_tiles_m);
+      const int z = (int)(tile / mn_tiles);
+      const long tmn = tile % mn_tiles;
+      const int tn = (int)(tmn / a.n_tiles_m), tm = (int)(tmn % a.n_tiles_m);
       const int nres = res_blocks(a, tm);
+      float* __restrict__ out = a.out ? a.out + (long)z * a.split_stride : nullptr;
       if (!mbar_wait(&tfull[acc], acc_phase, abort_flag, a.status)) break;
       fence_after();
       // residual tiles in shared memory: acquire the TMA writes
@@ -461,14 +483,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint4 hv, lv;
             __nv_bfloat16* hp = reinterpret_cast<__nv_bfloat16*>(&hv);
             __nv_bfloat16* lp = reinterpret_cast<__nv_bfloat16*>(&lv);
+            float yv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const float o = tanhf(v[j] + uu[j] + (bias ? bias[fb + j] : 0.f)) + res[j];
+              yv[j] = tanhf(v[j] + uu[j] + (bias ? bias[fb + j] : 0.f));
+              const float o = yv[j] + res[j];
               hp[j] = __float2bfloat16_rn(o);
               lp[j] = __float2bfloat16_rn(o - __bfloat162float(hp[j]));
             }
             *reinterpret_cast<uint4*>(oh + r * ldb + fb) = hv;
             if (ol) *reinterpret_cast<uint4*>(ol + r * ldb + fb) = lv;
+            if (a.y_out) {
+              float* yd = a.y_out + r * a.ldy + fb;
+              reinterpret_cast<float4*>(yd)[0] = make_float4(yv[0], yv[1], yv[2], yv[3]);
+              reinterpret_cast<float4*>(yd)[1] = make_float4(yv[4], yv[5], yv[6], yv[7]);
+            }
           }
         }
       } else if (a.mode == 2) {
@@ -713,11 +742,15 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
   if (a.rm && (a.mode == 1 || (a.mode == 2 && (a.mfeat % 8 || a.ldu % 4 || a.ldhb % 8)) ||
                (a.mode == 0 && (a.hb_hi ? a.ldhb % 8 : a.ldo % 4))))
     return FN_EINVAL;
+  if (a.ksplit > 1 && (a.nseg != 1 || a.mode != 0 || a.rm || a.res_smem || !a.out || a.kb_per_split < 1 ||
+                       (long)(a.ksplit - 1) * a.kb_per_split >= a.kblocks[0] || a.split_stride < 1))
+    return FN_EINVAL;
+  if (a.y_out && (!a.rm || a.mode != 2 || a.ldy % 4 || ((uintptr_t)a.y_out & 15))) return FN_EINVAL;
   for (int sg = 0; sg < a.nseg; ++sg) {
     if (a.seg_terms[sg] < 1 || a.seg_terms[sg] > 3 || a.kblocks[sg] < 1) return FN_EINVAL;
     if (a.seg_group[sg] && (a.seg_group[sg] % 8 || a.tile_n % a.seg_group[sg] || a.u_div < 1)) return FN_EINVAL;
   }
-  const long total = (long)a.n_tiles_n * a.n_tiles_m;
+  const long total = (long)a.n_tiles_n * a.n_tiles_m * (a.ksplit > 1 ? a.ksplit : 1);
   if (total <= 0) return FN_OK;
   int grid = device_sm_count();
   if (total < grid) grid = (int)total;
@@ -757,5 +790,35 @@ extern "C" fn_status ferminet_diag_bf16_gemm(const void* d_A, const void* d_B, f
   a.ldo = M;
   a.bias_period = 1;
   a.status = d_status;
+  return tc_gemm_launch((cudaStream_t)stream, a);
+}
+
+extern "C" fn_status ferminet_diag_bf16_gemm_splitk(const void* d_A, const void* d_B, float* d_C, int M, int N,
+                                                    int K, int tile_n, int ksplit, void* stream,
+                                                    unsigned* d_status) {
+  using namespace fn;
+  if (!d_A || !d_B || !d_C || !d_status || M < 1 || N < 1 || K < 1 || K % BK || ksplit < 1) return FN_EINVAL;
+  TcGemmArgs a{};
+  if (!tc_make_map(&a.A[0][0], d_A, M, K, BM) || !tc_make_map(&a.B[0][0], d_B, N, K, tile_n)) return FN_EINVAL;
+  a.A[0][1] = a.A[0][0];
+  a.B[0][1] = a.B[0][0];
+  a.kblocks[0] = K / BK;
+  a.seg_terms[0] = 1;
+  a.nseg = 1;
+  a.terms = 1;
+  a.rows = N;
+  a.mfeat = M;
+  a.tile_n = tile_n;
+  a.n_tiles_n = (N + tile_n - 1) / tile_n;
+  a.n_tiles_m = (M + BM - 1) / BM;
+  a.mode = 0;
+  a.out = d_C;
+  a.ldo = M;
+  a.bias_period = 1;
+  a.ksplit = ksplit;
+  a.kb_per_split = (K / BK + ksplit - 1) / ksplit;
+  a.split_stride = (long)N * M;
+  a.status = d_status;
+  if (ksplit > 1 && (long)(ksplit - 1) * a.kb_per_split >= K / BK) return FN_EINVAL;
   return tc_gemm_launch((cudaStream_t)stream, a);
 }

@@ -47,6 +47,15 @@ struct TcGemmArgs {
   __nv_bfloat16* hb_hi;   // output h^{l+1} as BF16 hi + lo: the operands of the
   __nv_bfloat16* hb_lo;   // next GEMM and the stored activation (lo may be null)
   long ldhb;
+  // split-K (mode 0, features on M, one segment): the k-blocks are cut into
+  // ksplit ranges of kb_per_split; range z accumulates its own tile and stores
+  // it at out + z * split_stride (ksplit <= 1: no split)
+  int ksplit, kb_per_split;
+  long split_stride;
+  // mode 2, rows on lanes: when set, the tanh values (before the residual) are
+  // also stored as FP32 [rows][ldy]
+  float* y_out;
+  long ldy;
   unsigned* status;
 };
 

@@ -114,3 +114,28 @@ def test_autotune_and_tuning_roundtrip():
     from paper_2011_07125_gb300.binding import FermiNetError
     with pytest.raises(FermiNetError):
         fn.set_tuning(feature_tile=100)
+
+
+@pytest.mark.parametrize("name,per", [("li", 16), ("ne", 8), ("c4h6", 2), ("c4h4x8", 1)])
+def test_mixed_logpsi_vjp_blocks(name, per):
+    """The adjoint of a mixed context on the tensor cores (stored value pass and
+    every contraction with BF16 hi + lo operands) against the oracle, block by
+    block, and against the same context's FP32 SIMT adjoint."""
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P, "mixed")
+    seeds = np.random.default_rng(3).standard_normal(x.shape[0]).astype(np.float32)
+    xx, ss = torch.from_numpy(x).cuda(), torch.from_numpy(seeds).cuda()
+    g_tc = fn.logpsi_vjp(xx, ss).cpu().numpy().astype(np.float64)
+    fn.set_tuning(adjoint_simt=1)
+    g_simt = fn.logpsi_vjp(xx, ss).cpu().numpy().astype(np.float64)
+    assert fn.sync() == "FN_OK"
+    g_o = oracle.logpsi_vjp(wl.net, P, wl.geoms, x, seeds, geo=geo)
+    err = np.linalg.norm(g_tc - g_o) / np.linalg.norm(g_o)
+    err_s = np.linalg.norm(g_simt - g_o) / np.linalg.norm(g_o)
+    print(name, "tensor-core adjoint rel L2", err, "SIMT adjoint", err_s)
+    for e in lay:  # block by block, so a misplaced block is named
+        sl = slice(e.offset, e.offset + e.count)
+        nb = np.linalg.norm(g_o[sl])
+        if nb > 1e-6 * np.linalg.norm(g_o):
+            assert np.linalg.norm(g_tc[sl] - g_o[sl]) / nb < TOL_GRAD_MIXED, e.name
+    assert err < 0.1 * TOL_GRAD_MIXED

@@ -39,3 +39,32 @@ def test_bf16_gemm_matches_torch(M, N, K, tile_n, rm):
     err = (Cm - ref).abs().max().item()
     scale = ref.abs().max().item()
     assert err <= 1e-5 * scale * (K ** 0.5), (err, scale)
+
+
+@pytest.mark.parametrize("M,N,K,tile_n,ks", [(256, 256, 64 * 40, 256, 7), (40, 256, 64 * 9, 256, 9),
+                                             (64, 448, 64 * 33, 224, 5), (512, 96, 64 * 3, 96, 3)])
+def test_bf16_gemm_splitk_partials(M, N, K, tile_n, ks):
+    """Split-K partials (the weight-gradient contractions of the adjoint):
+    each range's partial equals the matmul over its own k-blocks."""
+    from paper_2011_07125_gb300 import binding
+    f = binding.load().ferminet_diag_bf16_gemm_splitk
+    vp = C.c_void_p
+    f.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
+    f.restype = C.c_int
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    Cm = torch.full((ks, N, M), float("nan"), device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = f(A.data_ptr(), B.data_ptr(), Cm.data_ptr(), M, N, K, tile_n, ks,
+           C.c_void_p(torch.cuda.current_stream().cuda_stream), st.data_ptr())
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    kb = K // 64
+    kps = (kb + ks - 1) // ks
+    for z in range(ks):
+        k0, k1 = 64 * z * kps, 64 * min(kb, (z + 1) * kps)
+        ref = B[:, k0:k1].float() @ A[:, k0:k1].float().T
+        err = (Cm[z] - ref).abs().max().item()
+        assert err <= 1e-5 * max(ref.abs().max().item(), 1.0) * ((k1 - k0) ** 0.5), (z, err)
