@@ -29,7 +29,7 @@ _lib = None
 
 class ONet(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("d1", C.c_int), ("d2", C.c_int), ("n_det", C.c_int),
-                ("n_up", C.c_int), ("n_down", C.c_int), ("n_nuc", C.c_int)]
+                ("n_up", C.c_int), ("n_down", C.c_int), ("n_nuc", C.c_int), ("envelope", C.c_int)]
 
 
 class OEntry(C.Structure):
@@ -105,7 +105,8 @@ def _dp(a: np.ndarray):
 
 
 def _net(net) -> ONet:
-    return ONet(net.n_layers, net.d1, net.d2, net.n_det, net.n_up, net.n_down, net.n_nuc)
+    return ONet(net.n_layers, net.d1, net.d2, net.n_det, net.n_up, net.n_down, net.n_nuc,
+                int(getattr(net, "envelope", 0)))
 
 
 def _geo_arrays(geoms, n_nuc):

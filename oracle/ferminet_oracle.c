@@ -40,11 +40,14 @@
 /* Network shape and parameter layout                                        */
 /* ------------------------------------------------------------------------ */
 
+/* envelope 0: isotropic, exp(-|sigma| |r - R_m|) with one scalar sigma per
+ * (k, spin, i, m) (Sec. 3); envelope 1: full covariance, exp(-|Sigma (r - R_m)|)
+ * with one 3x3 matrix Sigma per (k, spin, i, m) (Eq. 4), stored row-major. */
 typedef struct {
-  int n_layers, d1, d2, n_det, n_up, n_down, n_nuc;
+  int n_layers, d1, d2, n_det, n_up, n_down, n_nuc, envelope;
 } onet;
 
-enum { O_INIT_NORMAL = 0, O_INIT_ZERO = 1, O_INIT_ONE = 2 };
+enum { O_INIT_NORMAL = 0, O_INIT_ZERO = 1, O_INIT_ONE = 2, O_INIT_EYE3 = 3 };
 
 typedef struct {
   char name[32];
@@ -63,13 +66,26 @@ static int din1_of(const onet* t, int l) { return l == 0 ? 4 * t->n_nuc : t->d1;
 static int din2_of(const onet* t, int l) { return l == 0 ? 4 : t->d2; }
 static int nspin(const onet* t, int s) { return s == 0 ? t->n_up : t->n_down; }
 
+/* One envelope term of Eq. 4 for displacement d = r_j - R_m: exp(-|sigma| |d|)
+ * (isotropic, sg[0] = sigma) or exp(-|Sigma d|) (full, sg = Sigma row-major). */
+static double env_term(const onet* t, const double* sg, const double d[3]) {
+  if (!t->envelope) return exp(-fabs(sg[0]) * sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  double v2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double va = sg[3 * a] * d[0] + sg[3 * a + 1] * d[1] + sg[3 * a + 2] * d[2];
+    v2 += va * va;
+  }
+  return exp(-sqrt(v2));
+}
+
 /* Layout, in this order:
  *   for each layer l: V_l [d1][3*din1 + 2*din2], b_l [d1],
  *                     and for l < L-1: W_l [d2][din2], c_l [d2]
  *   w_orb_up [K][n_up][d1], w_orb_down [K][n_down][d1],
  *   g_orb_up [K][n_up], g_orb_down [K][n_down],
  *   pi_up [K][n_up][N], pi_down [K][n_down][N],
- *   sigma_up [K][n_up][N], sigma_down [K][n_down][N].
+ *   sigma_up [K][n_up][N], sigma_down [K][n_down][N] (isotropic), or
+ *   [K][n_up][N][3][3], [K][n_down][N][3][3] (full covariance, identity init).
  * V_l acts on g_i = [h_i, mean_up h, mean_down h, mean_up h_i., mean_down h_i.]. */
 static int build_layout(const onet* t, olayout* L, oentry* ent, int max_ent) {
   long off = 0;
@@ -102,8 +118,10 @@ static int build_layout(const onet* t, olayout* L, oentry* ent, int max_ent) {
   ADD(L->g_orb[1], "g_orb_down", K * t->n_down, 1, O_INIT_ZERO);
   ADD(L->pi[0], "pi_up", K * t->n_up * t->n_nuc, 1, O_INIT_ONE);
   ADD(L->pi[1], "pi_down", K * t->n_down * t->n_nuc, 1, O_INIT_ONE);
-  ADD(L->sigma[0], "sigma_up", K * t->n_up * t->n_nuc, 1, O_INIT_ONE);
-  ADD(L->sigma[1], "sigma_down", K * t->n_down * t->n_nuc, 1, O_INIT_ONE);
+  const long sz = t->envelope ? 9 : 1;
+  const int skind = t->envelope ? O_INIT_EYE3 : O_INIT_ONE;
+  ADD(L->sigma[0], "sigma_up", K * t->n_up * t->n_nuc * sz, 1, skind);
+  ADD(L->sigma[1], "sigma_down", K * t->n_down * t->n_nuc * sz, 1, skind);
 #undef ADD
   L->total = off;
   return ne;
@@ -111,7 +129,8 @@ static int build_layout(const onet* t, olayout* L, oentry* ent, int max_ent) {
 
 static int check_net(const onet* t) {
   if (t->n_layers < 1 || t->n_layers > 16 || t->d1 < 1 || t->d2 < 1 || t->n_det < 1 ||
-      t->n_up < 0 || t->n_down < 0 || t->n_up + t->n_down < 1 || t->n_nuc < 1)
+      t->n_up < 0 || t->n_down < 0 || t->n_up + t->n_down < 1 || t->n_nuc < 1 || t->envelope < 0 ||
+      t->envelope > 1)
     return -1;
   return 0;
 }
@@ -372,7 +391,8 @@ static void oracle_fwd(const onet* t, const olayout* Lo, const double* P, const 
           double en = 0.0;
           for (int m = 0; m < N; ++m) {
             size_t pm = ((size_t)k * ns + i) * N + m;
-            en += pi[pm] * exp(-fabs(sg[pm]) * f->dist[(j0 + j) * N + m]);
+            const double* dv = f->h[0] + (size_t)(j0 + j) * 4 * N + 4 * m;  /* r_j - R_m */
+            en += pi[pm] * env_term(t, sg + pm * (t->envelope ? 9 : 1), dv);
           }
           f->orb[s][k * mat + i * ns + j] = o;
           f->env[s][k * mat + i * ns + j] = en;
@@ -436,14 +456,31 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
             G[Lo->w_orb[s] + ((size_t)k * ns + i) * d1 + q] += obar * f->h[L][(size_t)(j0 + j) * d1 + q];
             hbar[(size_t)(j0 + j) * d1 + q] += obar * w[((size_t)k * ns + i) * d1 + q];
           }
-          /* env = sum_m pi exp(-|sigma| r) */
+          /* env = sum_m pi exp(-|sigma| r), or sum_m pi exp(-|Sigma d|) */
           for (int m = 0; m < N; ++m) {
             size_t pm = ((size_t)k * ns + i) * N + m;
-            double r = f->dist[(j0 + j) * N + m];
-            double ex = exp(-fabs(sg[pm]) * r);
-            double sgn = sg[pm] > 0 ? 1.0 : (sg[pm] < 0 ? -1.0 : 0.0);
-            G[Lo->pi[s] + pm] += ebar * ex;
-            G[Lo->sigma[s] + pm] += ebar * pi[pm] * ex * (-r) * sgn;
+            if (!t->envelope) {
+              double r = f->dist[(j0 + j) * N + m];
+              double ex = exp(-fabs(sg[pm]) * r);
+              double sgn = sg[pm] > 0 ? 1.0 : (sg[pm] < 0 ? -1.0 : 0.0);
+              G[Lo->pi[s] + pm] += ebar * ex;
+              G[Lo->sigma[s] + pm] += ebar * pi[pm] * ex * (-r) * sgn;
+            } else {
+              /* v = Sigma d, rho = |v|: d exp(-rho) / d Sigma_ab = -exp(-rho) v_a d_b / rho */
+              const double* dv = f->h[0] + (size_t)(j0 + j) * 4 * N + 4 * m;
+              const double* S = sg + pm * 9;
+              double v[3], rho2 = 0.0;
+              for (int a = 0; a < 3; ++a) {
+                v[a] = S[3 * a] * dv[0] + S[3 * a + 1] * dv[1] + S[3 * a + 2] * dv[2];
+                rho2 += v[a] * v[a];
+              }
+              const double rho = sqrt(rho2), ex = exp(-rho);
+              G[Lo->pi[s] + pm] += ebar * ex;
+              if (rho > 0.0)
+                for (int a = 0; a < 3; ++a)
+                  for (int b = 0; b < 3; ++b)
+                    G[Lo->sigma[s] + pm * 9 + 3 * a + b] += ebar * pi[pm] * ex * (-v[a] * dv[b] / rho);
+            }
           }
         }
     }
@@ -589,6 +626,7 @@ static jet oracle_fwd_jet(const onet* t, const olayout* Lo, const double* P, con
   jet* xr = malloc(sizeof(jet) * 3 * n);
   for (int q = 0; q < 3 * n; ++q) { xr[q] = jc(x[q]); if (q == seed_coord) xr[q].d = 1.0; }
   jet* dist = malloc(sizeof(jet) * n * N);
+  jet* disp = malloc(sizeof(jet) * n * N * 3);  /* r_i - R_I, for the full-covariance envelope */
   int maxw = 4 * N > t->d1 ? 4 * N : t->d1;
   int maxw2 = t->d2 > 4 ? t->d2 : 4;
   jet* h = calloc((size_t)n * maxw, sizeof(jet));
@@ -601,6 +639,7 @@ static jet oracle_fwd_jet(const onet* t, const olayout* Lo, const double* P, con
       for (int a = 0; a < 3; ++a) { d[a] = jsub(xr[3 * i + a], jc(R[3 * I + a])); r2 = jadd(r2, jmul(d[a], d[a])); }
       jet r = jsqrt(r2);
       dist[i * N + I] = r;
+      for (int a = 0; a < 3; ++a) disp[((size_t)i * N + I) * 3 + a] = d[a];
       for (int a = 0; a < 3; ++a) h[(size_t)i * 4 * N + 4 * I + a] = d[a];
       h[(size_t)i * 4 * N + 4 * I + 3] = r;
     }
@@ -677,7 +716,18 @@ static jet oracle_fwd_jet(const onet* t, const olayout* Lo, const double* P, con
           jet env = jc(0.0);
           for (int m = 0; m < N; ++m) {
             size_t pm = ((size_t)k * ns + i) * N + m;
-            env = jadd(env, jscale(jexp(jscale(dist[(j0 + j) * N + m], -fabs(sg[pm]))), pi[pm]));
+            if (!t->envelope) {
+              env = jadd(env, jscale(jexp(jscale(dist[(j0 + j) * N + m], -fabs(sg[pm]))), pi[pm]));
+            } else {
+              const double* S = sg + pm * 9;
+              const jet* dv = disp + ((size_t)(j0 + j) * N + m) * 3;
+              jet rho2 = jc(0.0);
+              for (int a = 0; a < 3; ++a) {
+                jet va = jadd(jadd(jscale(dv[0], S[3 * a]), jscale(dv[1], S[3 * a + 1])), jscale(dv[2], S[3 * a + 2]));
+                rho2 = jadd(rho2, jmul(va, va));
+              }
+              env = jadd(env, jscale(jexp(jscale(jsqrt(rho2), -1.0)), pi[pm]));
+            }
           }
           A[i * ns + j] = jmul(o, env);
         }
@@ -700,7 +750,7 @@ static jet oracle_fwd_jet(const onet* t, const olayout* Lo, const double* P, con
     *sign_out = acc.v > 0 ? 1.0 : (acc.v < 0 ? -1.0 : 0.0);
     out = acc.v == 0.0 ? jc(-INFINITY) : jadd(lk[kmax], jlogabs(acc));
   }
-  free(lk); free(sk); free(xr); free(dist); free(h); free(hn); free(e); free(en);
+  free(lk); free(sk); free(xr); free(dist); free(disp); free(h); free(hn); free(e); free(en);
   return out;
 }
 

@@ -26,6 +26,7 @@ import numpy as np
 INIT_NORMAL = 0   # N(0, 1/fan_in)
 INIT_ZERO = 1     # biases
 INIT_ONE = 2      # envelope weights pi and exponents sigma ("exponents 1.0")
+INIT_EYE3 = 3     # full-covariance envelope matrices: 3x3 identities (row-major)
 
 # Seeds of the standard workloads: parameters 0, walkers 1, Metropolis 2.
 SEED_PARAMS = 0
@@ -43,6 +44,7 @@ class Net:
     n_up: int
     n_down: int
     n_nuc: int
+    envelope: int = 0  # 0: isotropic sigma (Sec. 3); 1: full 3x3 covariance (Eq. 4)
 
     @property
     def n_elec(self) -> int:
@@ -90,6 +92,10 @@ def init_params(layout: Sequence, seed: int = SEED_PARAMS) -> np.ndarray:
             chunks.append(np.zeros(cnt))
         elif e.kind == INIT_ONE:
             chunks.append(np.ones(cnt))
+        elif e.kind == INIT_EYE3:
+            if cnt % 9:
+                raise ValueError("a block of 3x3 identities needs a multiple of 9 entries")
+            chunks.append(np.tile(np.eye(3).reshape(-1), cnt // 9))
         else:
             raise ValueError(f"unknown init kind {e.kind}")
     if not chunks:

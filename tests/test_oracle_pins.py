@@ -429,3 +429,116 @@ def test_adapt_width_cases():
     assert oracle.adapt_width(0.02, 40, 100, 0.5, 0.55, 1.1) == pytest.approx(0.02 / 1.1, rel=1e-15)
     assert oracle.adapt_width(0.02, 52, 100, 0.5, 0.55, 1.1) == 0.02
     assert oracle.adapt_width(0.02, 0, 0, 0.5, 0.55, 1.1) == 0.02
+
+
+# ---------------------------------------------------------------------------
+# Full-covariance envelope (Eq. 4: one 3x3 Sigma per orbital and nucleus)
+# ---------------------------------------------------------------------------
+
+def _rotation(rng):
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    return q * np.sign(np.diag(r))
+
+
+def test_full_covariance_with_scaled_rotations_is_isotropic():
+    """Sigma = s Q with Q orthogonal gives |Sigma d| = |s| |d|: the
+    full-covariance network equals the isotropic one with sigma = s in log|psi|,
+    its derivatives and E_L, and its Sigma gradient contracted with Q is the
+    isotropic sigma gradient (chain rule through Sigma = s Q)."""
+    rng = np.random.default_rng(41)
+    iso = synth.Net(2, 12, 6, 2, 2, 1, 2)
+    full = synth.Net(2, 12, 6, 2, 2, 1, 2, envelope=1)
+    lay_i, P_i = _params(iso, 42)
+    lay_f = oracle.layout(full)
+    assert [e.name for e in lay_i] == [e.name for e in lay_f]
+    P_f = np.zeros(sum(e.count for e in lay_f))
+    Qs = {}
+    for ei, ef in zip(lay_i, lay_f):
+        blk = P_i[ei.offset:ei.offset + ei.count]
+        if ei.name.startswith("sigma_"):
+            blk[:] = 0.4 + rng.random(ei.count)
+            P_i[ei.offset:ei.offset + ei.count] = blk
+            Q = np.stack([_rotation(rng) for _ in range(ei.count)])
+            Qs[ei.name] = Q
+            P_f[ef.offset:ef.offset + ef.count] = (blk[:, None, None] * Q).reshape(-1)
+        else:
+            assert ei.count == ef.count
+            P_f[ef.offset:ef.offset + ef.count] = blk
+    geom = synth.Geometry(R=np.array([[0.0, 0.0, 0.0], [0.3, 1.2, -0.4]]), Z=np.array([2.0, 1.0]))
+    x = rng.standard_normal((4, 3, 3))
+    oi = oracle.local_energy(iso, P_i, [geom], x)
+    of = oracle.local_energy(full, P_f, [geom], x)
+    for k in ("logpsi", "sign", "eloc", "kinetic"):
+        np.testing.assert_allclose(of[k], oi[k], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(of["grad"], oi["grad"], rtol=1e-9, atol=1e-9)
+    seeds = np.array([0.3, -0.8, 1.1, 0.5])
+    gi = oracle.logpsi_vjp(iso, P_i, [geom], x, seeds)
+    gf = oracle.logpsi_vjp(full, P_f, [geom], x, seeds)
+    for ei, ef in zip(lay_i, lay_f):
+        a = gi[ei.offset:ei.offset + ei.count]
+        b = gf[ef.offset:ef.offset + ef.count]
+        if ei.name.startswith("sigma_"):
+            b = (b.reshape(-1, 3, 3) * Qs[ei.name]).sum(axis=(1, 2))
+        np.testing.assert_allclose(b, a, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(gi).max()), err_msg=ei.name)
+
+
+def test_full_covariance_hydrogen_closed_form():
+    """psi = exp(-|S r|) (one electron, Z = 1, w = 0, g = 1, pi = 1): with
+    M = S^T S, u = M r and rho = |S r|, the Laplacian of psi over psi is
+    |u|^2 / rho^2 - tr(M) / rho + |u|^2 / rho^3, so
+    E_L = -1/2 (that) - 1/|r| at every point."""
+    net = synth.Net(1, 4, 4, 1, 1, 0, 1, envelope=1)
+    lay, P = _params(net, 43)
+    _set(lay, P, "w_orb", 0.0)
+    _set(lay, P, "g_orb", 1.0)
+    S = np.array([[1.3, 0.2, -0.1], [0.0, 0.7, 0.4], [0.3, -0.2, 1.9]])
+    _block(lay, P, "sigma_up")[:] = S.reshape(-1)
+    x = np.random.default_rng(44).standard_normal((16, 1, 3))
+    out = oracle.local_energy(net, P, [synth.atom(1)], x)
+    r = x[:, 0]
+    M = S.T @ S
+    u = r @ M.T
+    rho = np.linalg.norm(r @ S.T, axis=1)
+    uu = (u ** 2).sum(axis=1)
+    lap = uu / rho ** 2 - np.trace(M) / rho + uu / rho ** 3
+    want = -0.5 * lap - 1.0 / np.linalg.norm(r, axis=1)
+    np.testing.assert_allclose(out["eloc"], want, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(out["logpsi"], -rho, rtol=1e-12)
+
+
+def test_full_covariance_derivatives_and_parameter_gradient_by_differences():
+    """Jets and the reverse pass of a full-covariance network against central
+    differences (coordinates and random parameter directions, block by block)."""
+    net = synth.Net(2, 10, 6, 2, 2, 2, 2, envelope=1)
+    lay, P = _params(net, 45)
+    rng = np.random.default_rng(46)
+    for e in lay:
+        if e.name.startswith("sigma_"):
+            P[e.offset:e.offset + e.count] += 0.3 * rng.standard_normal(e.count)
+        if e.name.startswith(("pi_", "g_orb")):
+            P[e.offset:e.offset + e.count] = 0.5 + rng.random(e.count)
+    geom = synth.Geometry(R=np.array([[0.0, 0.0, 0.0], [1.0, 0.5, 0.2]]), Z=np.array([2.0, 2.0]))
+    x = rng.standard_normal((2, 4, 3))
+    out = oracle.local_energy(net, P, [geom], x[:1])
+    h = 1e-4
+    lp0, _ = oracle.logpsi(net, P, [geom], x[:1])
+    for c in range(12):
+        xp = x[:1].copy().reshape(-1)
+        xm = x[:1].copy().reshape(-1)
+        xp[c] += h
+        xm[c] -= h
+        lpp, _ = oracle.logpsi(net, P, [geom], xp.reshape(1, 4, 3))
+        lpm, _ = oracle.logpsi(net, P, [geom], xm.reshape(1, 4, 3))
+        assert abs((lpp[0] - lpm[0]) / (2 * h) - out["grad"][0, c]) < 1e-6 * max(1, abs(out["grad"][0, c]))
+        fd2 = (lpp[0] - 2 * lp0[0] + lpm[0]) / h ** 2
+        assert abs(fd2 - out["d2"][0, c]) < 1e-3 * max(1, abs(fd2))
+    seeds = np.array([0.9, -0.6])
+    g = oracle.logpsi_vjp(net, P, [geom], x, seeds)
+    for e in lay:
+        v = np.zeros(P.shape[0])
+        v[e.offset:e.offset + e.count] = rng.standard_normal(e.count)
+        eps = 1e-6
+        lpp, _ = oracle.logpsi(net, P + eps * v, [geom], x)
+        lpm, _ = oracle.logpsi(net, P - eps * v, [geom], x)
+        fd = seeds @ ((lpp - lpm) / (2 * eps))
+        assert abs(fd - g @ v) < 2e-6 * max(1.0, abs(fd)), e.name
