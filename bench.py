@@ -404,6 +404,37 @@ def side_workload(name, flush, args):
     return res
 
 
+def envelope_overhead(flush, args):
+    """The full-covariance envelope (Eq. 4) against the isotropic one (Sec. 3)
+    on the C4H6 workload (the bicyclobutane stand-in of the paper's 40%
+    comparison): whole-step time of each, mixed precision."""
+    import dataclasses
+    import torch
+    from paper_2011_07125_gb300 import synth
+    from paper_2011_07125_gb300.binding import FermiNet
+    wl0 = synth.workload("c4h6")
+    x0 = synth.init_walkers(wl0)
+    res = {"workload": describe(wl0)}
+    for env in (0, 1):
+        wl = dataclasses.replace(wl0, net=dataclasses.replace(wl0.net, envelope=env))
+        fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision="mixed")
+        fn.set_params(torch.from_numpy(synth.init_params(fn.layout)).cuda())
+        x = torch.from_numpy(x0).cuda()
+        lp = fn.logpsi(x, with_sign=False)
+        if not args.no_autotune:
+            fn.autotune_cached(x, repeats=1)
+        fn.profile(True)
+        ms, _ = timed_steps(fn, wl, x, lp, 3, 2, flush, lambda f, xx, e: f.energy_grad(xx, e))
+        det = fn.profile_read("det_tangent")["ms"]
+        fn.profile(False)
+        res["full_covariance" if env else "isotropic"] = {
+            "ms_per_step": sum(ms) / len(ms), "value": wl.batch * len(ms) / (sum(ms) * 1e-3), "unit": UNIT,
+            "det_tangent_ms_per_step": det / len(ms), "status": fn.sync()}
+        fn.close()
+    res["full_over_isotropic_step_time"] = res["full_covariance"]["ms_per_step"] / res["isotropic"]["ms_per_step"]
+    return res
+
+
 def run_gpu(args, wl):
     import numpy as np
     import torch
@@ -579,7 +610,9 @@ def run_gpu(args, wl):
                            grad_fn=lambda: sample_context_grad(wl, prec, params, xs, cnt))
     if rank == 0 and world == 1 and args.side:
         for name in args.side.split(","):
-            if name and name != wl.name:
+            if name == "envelope":
+                side[name] = envelope_overhead(flush, args)
+            elif name and name != wl.name:
                 side[name] = side_workload(name, flush, args)
 
     if rank == 0:
@@ -651,8 +684,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "mixed"])
     ap.add_argument("--side", default=None,
-                    help="comma-separated workloads measured briefly after the main one (default: ne,ar with the "
-                         "default workload, none otherwise)")
+                    help="comma-separated workloads measured briefly after the main one, 'envelope' for the "
+                         "full-covariance against the isotropic envelope (default: ne,ar,envelope with the default "
+                         "workload, none otherwise)")
     ap.add_argument("--err-per-geom", type=int, default=16, help="walkers per geometry in the oracle error check")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -660,7 +694,7 @@ def main():
     ap.add_argument("--check-launch", action="store_true", help="host-only check of the rank launch, then exit")
     args = ap.parse_args()
     if args.side is None:
-        args.side = "ne,ar" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours" else ""
+        args.side = "ne,ar,envelope" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours" else ""
     if args.gpus < 1:
         sys.exit("--gpus must be at least 1")
     world = os.environ.get("WORLD_SIZE")

@@ -61,6 +61,9 @@ typedef enum {
  * geometry (all geometries of a context share it). */
 typedef struct {
   int n_layers, d1, d2, n_det, n_up, n_down, n_nuc;
+  int envelope;  /* 0: isotropic, exp(-|sigma| |r - R_m|) with a scalar sigma per
+                    (k, spin, i, m) (Sec. 3); 1: full covariance,
+                    exp(-|Sigma (r - R_m)|) with a 3x3 Sigma each (Eq. 4) */
 } fn_net;
 
 /* One nuclear geometry (host pointers): R [n_nuc][3] bohr, Z [n_nuc].
@@ -74,7 +77,8 @@ typedef struct {
 
 /* One block of the flat FP32 parameter vector.  kind: 0 = dense weight
  * (conventionally initialised N(0, 1/fan_in)), 1 = bias (0), 2 = envelope
- * weight pi or exponent sigma (1). */
+ * weight pi or isotropic exponent sigma (1), 3 = full-covariance envelope
+ * matrices (3x3 identities, row-major). */
 typedef struct {
   char name[32];
   long offset, count, fan_in;
@@ -98,7 +102,8 @@ fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms
  * a = 4 n_nuc or d1, e = 4 or d2), b_l [d1], and for l < L-1: W_l [d2][e],
  * c_l [d2]; then w_orb_up [K][n_up][d1], w_orb_down [K][n_down][d1],
  * g_orb_up [K][n_up], g_orb_down [K][n_down], pi_up / pi_down [K][n_s][n_nuc],
- * sigma_up / sigma_down [K][n_s][n_nuc]. */
+ * sigma_up / sigma_down [K][n_s][n_nuc] (isotropic envelope) or
+ * [K][n_s][n_nuc][3][3] (full covariance). */
 fn_status ferminet_param_layout(const fn_ctx* ctx, fn_param_entry* out, int max_entries, int* n_entries,
                                 long* n_params);
 

@@ -27,7 +27,7 @@ PREC = {"fp32": 0, "mixed": 1}
 
 class FnNet(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("d1", C.c_int), ("d2", C.c_int), ("n_det", C.c_int),
-                ("n_up", C.c_int), ("n_down", C.c_int), ("n_nuc", C.c_int)]
+                ("n_up", C.c_int), ("n_down", C.c_int), ("n_nuc", C.c_int), ("envelope", C.c_int)]
 
 
 class FnGeometry(C.Structure):
@@ -126,7 +126,8 @@ def load(path: Optional[str] = None):
 
 
 def _net(net) -> FnNet:
-    return FnNet(net.n_layers, net.d1, net.d2, net.n_det, net.n_up, net.n_down, net.n_nuc)
+    return FnNet(net.n_layers, net.d1, net.d2, net.n_det, net.n_up, net.n_down, net.n_nuc,
+                 int(getattr(net, "envelope", 0)))
 
 
 def net_layout(net) -> List[Entry]:

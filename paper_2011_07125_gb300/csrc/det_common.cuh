@@ -167,16 +167,49 @@ __device__ __forceinline__ MatId mat_id(long mat, const DetArgs& a) {
 }
 
 // Envelope of orbital i at electron jg, with its gradient along r_jg and its
-// Laplacian, in precision T.
+// Laplacian, in precision T.  Isotropic (Sec. 3): sum_m pi_m exp(-|sigma_m| r)
+// with r = |r_jg - R_m|.  Full covariance (Eq. 4): sum_m pi_m exp(-rho) with
+// v = Sigma_m d, rho = |v|, d = r_jg - R_m; with u = Sigma^T v (= M d for
+// M = Sigma^T Sigma) the gradient of exp(-rho) is -exp(-rho) u / rho and its
+// Laplacian exp(-rho) (|u|^2 / rho^2 - tr M / rho + |u|^2 / rho^3).
 template <class T>
 __device__ __forceinline__ void envelope(const DetArgs& a, const MatId& m, int i, int jg, const float* R, T& ev,
                                          T* eg, T& el, bool deriv) {
   const float* xj = a.x + (m.w * a.n + jg) * 3;
   const float* pi = a.pi[m.s] + ((long)m.k * m.ns + i) * a.N;
-  const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + i) * a.N;
   ev = T(0);
   el = T(0);
   eg[0] = eg[1] = eg[2] = T(0);
+  if (a.full_env) {
+    const float* S = a.sigma[m.s] + ((long)m.k * m.ns + i) * a.N * 9;
+    for (int mm = 0; mm < a.N; ++mm) {
+      const float* Sm = S + 9 * mm;
+      T d0 = (T)xj[0] - (T)R[3 * mm], d1 = (T)xj[1] - (T)R[3 * mm + 1], d2 = (T)xj[2] - (T)R[3 * mm + 2];
+      T v0 = (T)Sm[0] * d0 + (T)Sm[1] * d1 + (T)Sm[2] * d2;
+      T v1 = (T)Sm[3] * d0 + (T)Sm[4] * d1 + (T)Sm[5] * d2;
+      T v2 = (T)Sm[6] * d0 + (T)Sm[7] * d1 + (T)Sm[8] * d2;
+      T rho = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      T ex = (T)pi[mm] * exp(-rho);
+      ev += ex;
+      if (deriv) {
+        T u0 = (T)Sm[0] * v0 + (T)Sm[3] * v1 + (T)Sm[6] * v2;
+        T u1 = (T)Sm[1] * v0 + (T)Sm[4] * v1 + (T)Sm[7] * v2;
+        T u2 = (T)Sm[2] * v0 + (T)Sm[5] * v1 + (T)Sm[8] * v2;
+        T tr = T(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) tr += (T)Sm[q] * (T)Sm[q];
+        T ir = rho > T(0) ? T(1) / rho : T(0);
+        T uu = u0 * u0 + u1 * u1 + u2 * u2;
+        T gs = -ex * ir;
+        eg[0] = fma(gs, u0, eg[0]);
+        eg[1] = fma(gs, u1, eg[1]);
+        eg[2] = fma(gs, u2, eg[2]);
+        el = fma(ex, uu * ir * ir - tr * ir + uu * ir * ir * ir, el);
+      }
+    }
+    return;
+  }
+  const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + i) * a.N;
   for (int mm = 0; mm < a.N; ++mm) {
     T d0 = (T)xj[0] - (T)R[3 * mm], d1 = (T)xj[1] - (T)R[3 * mm + 1], d2 = (T)xj[2] - (T)R[3 * mm + 2];
     T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);

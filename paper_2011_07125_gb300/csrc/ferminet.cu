@@ -60,8 +60,12 @@ void build_layout(const fn_net& t, Layout* L, bool with_entries) {
   add(nullptr, "g_orb_down", K * t.n_down, 1, 1);
   add(&L->pi[0], "pi_up", K * t.n_up * t.n_nuc, 1, 2);
   add(&L->pi[1], "pi_down", K * t.n_down * t.n_nuc, 1, 2);
-  add(&L->sigma[0], "sigma_up", K * t.n_up * t.n_nuc, 1, 2);
-  add(&L->sigma[1], "sigma_down", K * t.n_down * t.n_nuc, 1, 2);
+  // isotropic: one scalar sigma per (k, spin, i, m), init 1; full covariance
+  // (Eq. 4): one row-major 3x3 Sigma each, init the identity (kind 3)
+  const long sz = t.envelope ? 9 : 1;
+  const int skind = t.envelope ? 3 : 2;
+  add(&L->sigma[0], "sigma_up", K * t.n_up * t.n_nuc * sz, 1, skind);
+  add(&L->sigma[1], "sigma_down", K * t.n_down * t.n_nuc * sz, 1, skind);
   L->total = off;
 }
 
@@ -640,6 +644,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
   da.pi[1] = P + c->lay.pi[1];
   da.sigma[0] = P + c->lay.sigma[0];
   da.sigma[1] = P + c->lay.sigma[1];
+  da.full_env = t.envelope;
   da.tangent = tangent;
   da.logdet = logdet;
   da.sign = sgn;
@@ -767,7 +772,8 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
   const int max_din1 = std::max(4 * N, d1), max_din2 = std::max(4, d2);
   const long ldk = pad64(rows), ldkw = pad64(Bc), lko = pad64(Ktot), ldh = pad64(d1), ldh0 = pad64(4 * N);
   float* Obar = ar.get<float>(rows * Ktot);
-  float* envg = ar.get<float>(Bc * 2 * Ktot * N);
+  const long env_cols = (t.envelope ? 10 : 2) * Ktot * N;  // pi part, then sigma part
+  float* envg = ar.get<float>(Bc * env_cols);
   float* Hbar[2] = {ar.get<float>(rows * max_din1), ar.get<float>(rows * max_din1)};
   float* Zbar = ar.get<float>(rows * d1);
   float* Ebar[2] = {ar.get<float>(pairs * max_din2), ar.get<float>(pairs * max_din2)};
@@ -789,7 +795,7 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
   auto part_need = [&](long Pn, long Qn, long Kk) { part_max = std::max(part_max, tn_ksplit(Pn, Qn, Kk) * Pn * Qn); };
   auto cs_need = [&](long r, long cl) { cs_max = std::max(cs_max, colsum_scratch_elems(r, cl)); };
   part_need(Ktot, d1, ldk);
-  cs_need(Bc, 2 * Ktot * N);
+  cs_need(Bc, env_cols);
   cs_need(rows, Ktot);
   for (int l = 0; l < L; ++l) {
     const int a1 = din1_of(t, l), a2 = din2_of(t, l);
@@ -834,10 +840,11 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
   ad.pi[1] = P + Lo.pi[1];
   ad.sigma[0] = P + Lo.sigma[0];
   ad.sigma[1] = P + Lo.sigma[1];
+  ad.full_env = t.envelope;
   ad.Obar = Obar;
   ad.envgrad = envg;
   launch_adj_det(s, ad);
-  launch_colsum_accum(s, envg, Bc, 2 * Ktot * N, 2 * Ktot * N, grad + Lo.pi[0], cs_scr);
+  launch_colsum_accum(s, envg, Bc, env_cols, env_cols, grad + Lo.pi[0], cs_scr);
   // orbital weights: grad[q][f] += sum_r Obar[r][q] h^L[r][f]
   launch_t_bf16(s, st.Hb[L][0], st.Hb[L][1], ldh, rows, d1, TA[0], TA[1], ldk);
   launch_t_split(s, Obar, Ktot, rows, Ktot, TB[0], TB[1], ldk);
@@ -925,7 +932,8 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
   forward(c, ar, x, Bc, w0, false, true, FwdOut{lp, nullptr, nullptr, nullptr}, &st);
   const int max_din1 = std::max(4 * N, d1), max_din2 = std::max(4, d2);
   float* Obar = ar.get<float>(rows * Ktot);
-  float* envg = ar.get<float>(Bc * 2 * Ktot * N);
+  const long env_cols = (t.envelope ? 10 : 2) * Ktot * N;  // pi part, then sigma part
+  float* envg = ar.get<float>(Bc * env_cols);
   float* Hbar[2] = {ar.get<float>(rows * max_din1), ar.get<float>(rows * max_din1)};
   float* Zbar = ar.get<float>(rows * d1);
   float* Ebar[2] = {ar.get<float>(pairs * max_din2), ar.get<float>(pairs * max_din2)};
@@ -940,7 +948,7 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
   };
   auto cs_need = [&](long r, long cl) { cs_max = std::max(cs_max, colsum_scratch_elems(r, cl)); };
   tn_need(Ktot, d1, rows);
-  cs_need(Bc, 2 * Ktot * N);
+  cs_need(Bc, env_cols);
   cs_need(rows, Ktot);
   for (int l = 0; l < L; ++l) {
     const int a1 = din1_of(t, l), a2 = din2_of(t, l);
@@ -986,10 +994,11 @@ void vjp_chunk(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const flo
   ad.pi[1] = P + Lo.pi[1];
   ad.sigma[0] = P + Lo.sigma[0];
   ad.sigma[1] = P + Lo.sigma[1];
+  ad.full_env = t.envelope;
   ad.Obar = Obar;
   ad.envgrad = envg;
   launch_adj_det(s, ad);
-  launch_colsum_accum(s, envg, Bc, 2 * Ktot * N, 2 * Ktot * N, grad + Lo.pi[0], cs_scr);
+  launch_colsum_accum(s, envg, Bc, env_cols, env_cols, grad + Lo.pi[0], cs_scr);
   TN(Ktot, d1, rows, Obar, Ktot, st.H[L], d1, grad + Lo.w_orb, d1);
   launch_colsum_accum(s, Obar, rows, Ktot, Ktot, grad + Lo.g_orb, cs_scr);
   gemm_nn(s, rows, d1, Ktot, Obar, Ktot, P + Lo.w_orb, d1, Hbar[0], d1, Epi{});
@@ -1353,7 +1362,8 @@ fn_status ferminet_init(const fn_net* net, const fn_geometry* geoms, int n_geoms
   if (!net || !geoms || n_geoms < 1) return FN_EINVAL;
   const fn_net& t = *net;
   if (t.n_layers < 1 || t.n_layers > 16 || t.d1 < 1 || t.d2 < 1 || t.d2 > 32 || t.n_det < 1 || t.n_up < 0 ||
-      t.n_down < 0 || t.n_up + t.n_down < 1 || t.n_up > 32 || t.n_down > 32 || t.n_nuc < 1)
+      t.n_down < 0 || t.n_up + t.n_down < 1 || t.n_up > 32 || t.n_down > 32 || t.n_nuc < 1 ||
+      t.envelope < 0 || t.envelope > 1)
     return FN_EINVAL;
   if (prec != FN_PREC_FP32 && prec != FN_PREC_MIXED) return FN_EINVAL;
   for (int g = 0; g < n_geoms; ++g)
@@ -1501,7 +1511,8 @@ fn_status ferminet_param_layout(const fn_ctx* c, fn_param_entry* out, int max_en
 fn_status ferminet_net_layout(const fn_net* net, fn_param_entry* out, int max_entries, int* n_entries,
                               long* n_params) {
   if (!net || net->n_layers < 1 || net->n_layers > 16 || net->d1 < 1 || net->d2 < 1 || net->n_det < 1 ||
-      net->n_up < 0 || net->n_down < 0 || net->n_up + net->n_down < 1 || net->n_nuc < 1)
+      net->n_up < 0 || net->n_down < 0 || net->n_up + net->n_down < 1 || net->n_nuc < 1 ||
+      net->envelope < 0 || net->envelope > 1)
     return FN_EINVAL;
   Layout L;
   build_layout(*net, &L);

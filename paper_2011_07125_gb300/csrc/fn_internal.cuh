@@ -190,7 +190,8 @@ struct DetArgs {
   Geo g;
   long w0, Bc;
   const float* pi[2];
-  const float* sigma[2];
+  const float* sigma[2];  // [K][n_s][N] scalars, or [K][n_s][N][3][3] with full_env
+  int full_env;           // 1: full-covariance envelope exp(-|Sigma (r - R_m)|)
   bool tangent;
   float* logdet;       // [Bc][K][2]
   float* sign;         // [Bc][K][2]
@@ -261,8 +262,9 @@ struct AdjDetArgs {
   int n, n_up, K, N, NS;
   const float* pi[2];
   const float* sigma[2];
+  int full_env;          // 1: sigma holds 3x3 matrices (9 gradient entries each)
   float* Obar;           // [Bc][n][Ktot]
-  float* envgrad;        // per walker [Bc][2][K*n*N] (pi part then sigma part)
+  float* envgrad;        // per walker [K*n*N] pi part, then [K*n*N*(9 or 1)] sigma part
 };
 void launch_adj_det(cudaStream_t s, const AdjDetArgs& a);
 // grad[c] += sum_r X[r * ldx + c] in FP64 (two-pass, deterministic);

@@ -43,23 +43,53 @@ __global__ void __launch_bounds__(128) k_adj_det(AdjDetArgs a) {
   const float* R = a.g.R + (long)geo_of(a.g, a.w0 + w) * a.N * 3;
   const long KnN = (long)a.K * a.n * a.N;
   const long pioff = s == 0 ? 0L : (long)a.K * a.n_up * a.N;
+  const int sz = a.full_env ? 9 : 1;
+  float* eg_w = a.envgrad + w * (1 + sz) * KnN;
   for (int t = threadIdx.x; t < ns * a.N; t += blockDim.x) {
     const int i = t / a.N, m = t % a.N;
     const long pm = ((long)k * ns + i) * a.N + m;
-    const float sg = a.sigma[s][pm], pv = a.pi[s][pm];
-    const float as = fabsf(sg), sgn = sg > 0.f ? 1.f : (sg < 0.f ? -1.f : 0.f);
-    float gp = 0.f, gs = 0.f;
-    for (int j = 0; j < ns; ++j) {
-      const float* xj = a.x + (w * a.n + j0 + j) * 3;
-      float d0 = xj[0] - R[3 * m], d1 = xj[1] - R[3 * m + 1], d2 = xj[2] - R[3 * m + 2];
-      float rr = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-      float ex = expf(-as * rr);
-      float eb = Eb[i * ns + j];
-      gp = fmaf(eb, ex, gp);
-      gs = fmaf(eb * pv * ex, -rr * sgn, gs);
+    const float pv = a.pi[s][pm];
+    if (a.full_env) {
+      // d exp(-rho) / d Sigma_ab = -exp(-rho) v_a d_b / rho, v = Sigma d
+      const float* S = a.sigma[s] + pm * 9;
+      float gp = 0.f, gS[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gS[q] = 0.f;
+      for (int j = 0; j < ns; ++j) {
+        const float* xj = a.x + (w * a.n + j0 + j) * 3;
+        const float d[3] = {xj[0] - R[3 * m], xj[1] - R[3 * m + 1], xj[2] - R[3 * m + 2]};
+        float v[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] = S[3 * q] * d[0] + S[3 * q + 1] * d[1] + S[3 * q + 2] * d[2];
+        const float rho = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const float ex = expf(-rho);
+        const float eb = Eb[i * ns + j];
+        gp = fmaf(eb, ex, gp);
+        const float c = rho > 0.f ? -eb * pv * ex / rho : 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) gS[3 * q + b] = fmaf(c * v[q], d[b], gS[3 * q + b]);
+      }
+      eg_w[pioff + pm] = gp;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) eg_w[KnN + (pioff + pm) * 9 + q] = gS[q];
+    } else {
+      const float sg = a.sigma[s][pm];
+      const float as = fabsf(sg), sgn = sg > 0.f ? 1.f : (sg < 0.f ? -1.f : 0.f);
+      float gp = 0.f, gs = 0.f;
+      for (int j = 0; j < ns; ++j) {
+        const float* xj = a.x + (w * a.n + j0 + j) * 3;
+        float d0 = xj[0] - R[3 * m], d1 = xj[1] - R[3 * m + 1], d2 = xj[2] - R[3 * m + 2];
+        float rr = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        float ex = expf(-as * rr);
+        float eb = Eb[i * ns + j];
+        gp = fmaf(eb, ex, gp);
+        gs = fmaf(eb * pv * ex, -rr * sgn, gs);
+      }
+      eg_w[pioff + pm] = gp;
+      eg_w[KnN + pioff + pm] = gs;
     }
-    a.envgrad[w * 2 * KnN + pioff + pm] = gp;
-    a.envgrad[w * 2 * KnN + KnN + pioff + pm] = gs;
   }
 }
 

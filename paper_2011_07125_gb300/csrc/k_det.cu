@@ -31,7 +31,7 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
   // determinant only, in FP32: half-warp LU and fast exponentials (the stored
   // forward of the adjoint keeps the accurate path)
   bool fast = false;
-  if constexpr (std::is_same<T, float>::value) fast = !a.minv && !a.env;
+  if constexpr (std::is_same<T, float>::value) fast = !a.minv && !a.env && !a.full_env;
 #pragma unroll
   for (int c = 0; c < NM; ++c) {
     ra[c] = (c == sl) ? T(1) : T(0);
@@ -60,6 +60,7 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
   } else if (sl < m.ns) {
     const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
     const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + sl) * a.N;
+    const float* R = a.g.R + (long)geo_of(a.g, a.w0 + m.w) * a.N * 3;
 #pragma unroll
     for (int c = 0; c < NM; ++c) {
       if (c < m.ns) {
@@ -67,7 +68,12 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
         const T o = (T)a.O[((m.w * a.n + jg) * (long)a.C) * a.ldo + m.q0 + sl];
         const float* dj = dist + jg * a.N;
         T ev = T(0);
-        for (int mm = 0; mm < a.N; ++mm) ev += (T)pi[mm] * exp(-fabs((T)sg[mm]) * (T)dj[mm]);
+        if (a.full_env) {
+          T eg[3], el;
+          envelope<T>(a, m, sl, jg, R, ev, eg, el, false);
+        } else {
+          for (int mm = 0; mm < a.N; ++mm) ev += (T)pi[mm] * exp(-fabs((T)sg[mm]) * (T)dj[mm]);
+        }
         ra[c] = o * ev;
         if (a.env) a.env[mat * NSS + sl * m.ns + c] = (float)ev;
       }

@@ -45,7 +45,7 @@ extern "C" fn_status ferminet_logpsi_noalloc(const fn_net* net, const float* d_p
                                              void* stream) {
   if (!net || net->n_layers < 1 || net->n_layers > 16 || net->d1 < 1 || net->d2 < 1 || net->d2 > 32 ||
       net->n_det < 1 || net->n_up < 0 || net->n_down < 0 || net->n_up + net->n_down < 1 || net->n_up > 32 ||
-      net->n_down > 32 || net->n_nuc < 1)
+      net->n_down > 32 || net->n_nuc < 1 || net->envelope < 0 || net->envelope > 1)
     return FN_EINVAL;
   if (B < 0) return FN_EINVAL;
   if (B == 0) return FN_OK;

@@ -37,14 +37,19 @@ def test_layout_matches_oracle(name):
            [(e.name, e.offset, e.count, e.fan_in, e.kind) for e in b]
 
 
-@pytest.mark.parametrize("shape", [(1, 4, 4, 1, 1, 0, 1), (3, 16, 8, 2, 2, 3, 2), (2, 32, 32, 4, 7, 7, 5)])
+@pytest.mark.parametrize("shape", [(1, 4, 4, 1, 1, 0, 1), (3, 16, 8, 2, 2, 3, 2), (2, 32, 32, 4, 7, 7, 5),
+                                   (1, 4, 4, 1, 1, 0, 1, 1), (2, 32, 32, 4, 7, 7, 5, 1)])
 def test_layout_matches_oracle_odd_shapes(shape):
+    """Odd shapes, with the isotropic and the full-covariance envelope."""
     net = synth.Net(*shape)
     a = binding.net_layout(net)
     b = oracle.layout(net)
-    assert [(e.name, e.offset, e.count) for e in a] == [(e.name, e.offset, e.count) for e in b]
+    assert [(e.name, e.offset, e.count, e.fan_in, e.kind) for e in a] == \
+           [(e.name, e.offset, e.count, e.fan_in, e.kind) for e in b]
 
 
 def test_invalid_shape_rejected():
     with pytest.raises(binding.FermiNetError):
         binding.net_layout(synth.Net(0, 4, 4, 1, 1, 1, 1))
+    with pytest.raises(binding.FermiNetError):
+        binding.net_layout(synth.Net(1, 4, 4, 1, 1, 1, 1, envelope=2))

@@ -1,0 +1,115 @@
+"""The full-covariance envelope of Eq. 4 (one 3x3 Sigma per orbital and
+nucleus) on the GPU against the oracle: log|psi|, the local energy and the
+parameter gradient, in both precisions, plus its reduction to the isotropic
+envelope (Sec. 3) when every Sigma is the identity."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_07125_gb300 import synth
+from helpers import (TOL_GRAD_MIXED, U_MIXED, eloc_bound, logpsi_bound, mixed_eloc_bound, rel_err)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD_FP32 = 1e-3
+
+
+def _case(name, per, seed=7):
+    wl = synth.workload(name)
+    wl = dataclasses.replace(wl, net=dataclasses.replace(wl.net, envelope=1),
+                             counts=[min(c, per) for c in wl.counts])
+    lay = oracle.layout(wl.net)
+    P = synth.init_params(lay)
+    rng = np.random.default_rng(seed)
+    for e in lay:  # anisotropic, sheared Sigma around the identity
+        if e.name.startswith("sigma_"):
+            P[e.offset:e.offset + e.count] += (0.25 * rng.standard_normal(e.count)).astype(np.float32)
+    x = synth.init_walkers(wl)
+    geo = synth.geometry_of_walkers(wl.counts)
+    return wl, lay, P, x, geo
+
+
+def _make(wl, P, prec):
+    from paper_2011_07125_gb300.binding import FermiNet
+    fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision=prec)
+    fn.set_params(torch.from_numpy(P).cuda())
+    return fn
+
+
+@pytest.mark.parametrize("name,per", [("li", 32), ("ne", 12), ("c4h6", 3), ("c4h4x8", 2)])
+def test_full_covariance_fp32_matches_oracle(name, per):
+    wl, lay, P, x, geo = _case(name, per)
+    fn = _make(wl, P, "fp32")
+    xx = torch.from_numpy(x).cuda()
+    out = fn.local_energy(xx)
+    lp, sg = fn.logpsi(xx)
+    seeds = np.random.default_rng(3).standard_normal(len(x)).astype(np.float32)
+    g = fn.logpsi_vjp(xx, torch.from_numpy(seeds).cuda()).cpu().numpy().astype(np.float64)
+    assert fn.sync() == "FN_OK"
+    ref = oracle.local_energy(wl.net, P, wl.geoms, x, geo=geo)
+    de = np.abs(out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"])
+    print(name, "full covariance: E_L max err", de.max(), "logpsi max rel", rel_err(lp.cpu().numpy(), ref["logpsi"]).max())
+    assert np.all(de <= eloc_bound(wl.net, ref)), (de / eloc_bound(wl.net, ref)).max()
+    assert np.all(np.abs(lp.cpu().numpy() - ref["logpsi"]) <= logpsi_bound(wl.net, ref))
+    assert np.array_equal(sg.cpu().numpy(), ref["sign"])
+    g_o = oracle.logpsi_vjp(wl.net, P, wl.geoms, x, seeds, geo=geo)
+    for e in lay:
+        sl = slice(e.offset, e.offset + e.count)
+        nb = np.linalg.norm(g_o[sl])
+        if nb > 1e-6 * np.linalg.norm(g_o):
+            assert np.linalg.norm(g[sl] - g_o[sl]) / nb < 1e-2, e.name
+    assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) < TOL_GRAD_FP32
+
+
+@pytest.mark.parametrize("name,per", [("c4h6", 3), ("c4h4x8", 1)])
+def test_full_covariance_mixed_matches_oracle(name, per):
+    wl, lay, P, x, geo = _case(name, per)
+    fn = _make(wl, P, "mixed")
+    xx = torch.from_numpy(x).cuda()
+    out = fn.local_energy(xx)
+    seeds = np.random.default_rng(4).standard_normal(len(x)).astype(np.float32)
+    g = fn.logpsi_vjp(xx, torch.from_numpy(seeds).cuda()).cpu().numpy().astype(np.float64)
+    assert fn.sync() == "FN_OK"
+    ref = oracle.local_energy(wl.net, P, wl.geoms, x, geo=geo)
+    de = np.abs(out["eloc"].cpu().numpy().astype(np.float64) - ref["eloc"])
+    assert np.all(de <= mixed_eloc_bound(wl.net, ref)), (de / mixed_eloc_bound(wl.net, ref)).max()
+    assert np.all(np.abs(out["logpsi"].cpu().numpy() - ref["logpsi"]) <= logpsi_bound(wl.net, ref, u=U_MIXED))
+    g_o = oracle.logpsi_vjp(wl.net, P, wl.geoms, x, seeds, geo=geo)
+    assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) < TOL_GRAD_MIXED
+
+
+def test_identity_covariance_is_the_isotropic_envelope():
+    """Sigma = I gives |Sigma d| = |d|: the same log|psi|, E_L and (pi, the
+    other blocks) gradient as the isotropic network with sigma = 1; the
+    isotropic sigma gradient is the trace of the Sigma gradient."""
+    wl = synth.subset(synth.workload("c4h6"), 3)
+    wf = dataclasses.replace(wl, net=dataclasses.replace(wl.net, envelope=1))
+    lay_i, lay_f = oracle.layout(wl.net), oracle.layout(wf.net)
+    P_i = synth.init_params(lay_i)
+    P_f = synth.init_params(lay_f)  # identity Sigma, every other block equal
+    for ei, ef in zip(lay_i, lay_f):
+        if not ei.name.startswith("sigma_"):
+            assert np.array_equal(P_i[ei.offset:ei.offset + ei.count], P_f[ef.offset:ef.offset + ef.count])
+    x = synth.init_walkers(wl)
+    xx = torch.from_numpy(x).cuda()
+    seeds = torch.linspace(-1, 1, len(x), device="cuda")
+    res = []
+    for w, P in ((wl, P_i), (wf, P_f)):
+        fn = _make(w, P, "fp32")
+        out = fn.local_energy(xx)
+        g = fn.logpsi_vjp(xx, seeds).cpu().numpy().astype(np.float64)
+        assert fn.sync() == "FN_OK"
+        res.append((out["logpsi"].cpu().numpy(), out["eloc"].cpu().numpy(), g))
+        fn.close()
+    (li, ei_, gi), (lf, ef_, gf) = res
+    np.testing.assert_allclose(lf, li, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(ef_, ei_, rtol=1e-4, atol=1e-4)
+    for bi, bf in zip(lay_i, lay_f):
+        a = gi[bi.offset:bi.offset + bi.count]
+        b = gf[bf.offset:bf.offset + bf.count]
+        if bi.name.startswith("sigma_"):
+            b = b.reshape(-1, 3, 3).trace(axis1=1, axis2=2)
+        np.testing.assert_allclose(b, a, rtol=2e-3, atol=2e-3 * max(1.0, np.abs(gi).max()), err_msg=bi.name)
