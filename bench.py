@@ -387,7 +387,9 @@ def side_workload(name, flush, args):
         lp = fn.logpsi(x, with_sign=False)
         if prec == "mixed" and not args.no_autotune:
             fn.autotune_cached(x, repeats=1)
-        ms, out = timed_steps(fn, wl, x, lp, 3, 2, flush, lambda f, xx, e: f.energy_grad(xx, e))
+        main = prec == wl.precision
+        ms, out = timed_steps(fn, wl, x, lp, 3 if main else 2, 2 if main else 1, flush,
+                              lambda f, xx, e: f.energy_grad(xx, e))
         st = fn.sync()
         v = wl.batch * len(ms) / (sum(ms) * 1e-3)
         res[prec] = {"value": v, "unit": UNIT, "ms_per_step": sum(ms) / len(ms), "status": st}
@@ -685,8 +687,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "mixed"])
     ap.add_argument("--side", default=None,
                     help="comma-separated workloads measured briefly after the main one, 'envelope' for the "
-                         "full-covariance against the isotropic envelope (default: ne,ar,envelope with the default "
-                         "workload, none otherwise)")
+                         "full-covariance against the isotropic envelope, name@B for another batch size "
+                         "(default: ne,ar,ar@16384,kr,envelope with the default workload, none otherwise)")
     ap.add_argument("--err-per-geom", type=int, default=16, help="walkers per geometry in the oracle error check")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -694,7 +696,8 @@ def main():
     ap.add_argument("--check-launch", action="store_true", help="host-only check of the rank launch, then exit")
     args = ap.parse_args()
     if args.side is None:
-        args.side = "ne,ar,envelope" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours" else ""
+        args.side = ("ne,ar,ar@16384,kr,envelope" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours"
+                     else "")
     if args.gpus < 1:
         sys.exit("--gpus must be at least 1")
     world = os.environ.get("WORLD_SIZE")

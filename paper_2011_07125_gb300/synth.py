@@ -196,7 +196,15 @@ def geometry_of_walkers(counts: Sequence[int]) -> np.ndarray:
 
 
 def workload(name: str) -> Workload:
-    """The five standard workloads (by system): li, ne, ar, c4h6, c4h4x8."""
+    """The standard workloads (by system): li, ne, ar, c4h6, c4h4x8, and kr (36
+    electrons at the Ar widths).  "name@B" sets the batch of a one-geometry
+    workload to B walkers."""
+    if "@" in name:
+        base, b = name.split("@", 1)
+        wl = workload(base)
+        if len(wl.geoms) != 1:
+            raise KeyError(name)
+        return dataclasses.replace(wl, name=name, counts=[int(b)])
     if name == "li":
         return Workload("li", Net(2, 32, 8, 1, 2, 1, 1), [atom(3)], [256], 1.0, 1, 0.02, "fp32", True)
     if name == "ne":
@@ -206,13 +214,15 @@ def workload(name: str) -> Workload:
     if name == "c4h6":
         return Workload("c4h6", Net(4, 256, 32, 16, 15, 15, 10), [c4h6_geometry(0)], [4096], 1.0, 10, 0.02,
                         "mixed", True)
+    if name == "kr":  # a larger electron count at the second-row widths: 36 electrons, 18 per spin
+        return Workload("kr", Net(4, 512, 32, 32, 18, 18, 1), [atom(36)], [4096], 1.5, 10, 0.02, "mixed", True)
     if name == "c4h4x8":
         return Workload("c4h4x8", Net(4, 256, 32, 16, 14, 14, 8), c4h4_geometries(8),
                         [256, 512, 768, 1024, 1536, 2048, 3072, 4096], 1.0, 10, 0.02, "mixed", True)
     raise KeyError(name)
 
 
-WORKLOADS = ("li", "ne", "ar", "c4h6", "c4h4x8")
+WORKLOADS = ("li", "ne", "ar", "c4h6", "c4h4x8", "kr")
 
 
 def subset(wl: Workload, per_geom: int) -> Workload:

@@ -22,7 +22,7 @@ TOL_GRAD_FP32 = 1e-3
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-CASES = [("li", None), ("ne", 24), ("ar", 6), ("c4h6", 4), ("c4h4x8", 2)]
+CASES = [("li", None), ("ne", 24), ("ar", 6), ("c4h6", 4), ("c4h4x8", 2), ("kr", 3)]
 
 
 def make(wl, P, precision="fp32"):

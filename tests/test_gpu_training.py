@@ -93,7 +93,9 @@ def test_width_adaptation_matches_oracle(width0):
     acc_b = fn.mcmc_step(xb, lb, 5, 123.0, 9, 40)  # the width argument is ignored
     assert fn.sync() == "FN_OK"
     assert torch.equal(xa, xb) and torch.equal(la, lb) and torch.equal(acc_a, acc_b)
-    want = oracle.adapt_width(np.float32(width0), int(acc_b.sum()), 64 * 5, 0.5, 0.55, 1.1)
+    # the library holds the band and the factor as float32
+    lo, hi, fac = (float(np.float32(v)) for v in (0.5, 0.55, 1.1))
+    want = oracle.adapt_width(np.float32(width0), int(acc_b.sum()), 64 * 5, lo, hi, fac)
     assert float(w.item()) == float(np.float32(want))
     # without an accepted-count buffer the library counts internally
     w2 = w.clone()
@@ -103,7 +105,7 @@ def test_width_adaptation_matches_oracle(width0):
     fn.lib.ferminet_mcmc_step(fn.ctx, xb.data_ptr(), lb.data_ptr(), 64, 3, 0.0, 9, 50, None)
     assert fn.sync() == "FN_OK"
     assert torch.equal(xa, xb) and torch.equal(w, w2)
-    want = oracle.adapt_width(float(np.float32(want)), int(acc_c.sum()), 64 * 3, 0.5, 0.55, 1.1)
+    want = oracle.adapt_width(float(np.float32(want)), int(acc_c.sum()), 64 * 3, lo, hi, fac)
     assert float(w.item()) == float(np.float32(want))
     fn.close()
 
