@@ -698,6 +698,8 @@ def main():
     if args.side is None:
         args.side = ("ne,ar,ar@16384,kr,envelope" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours"
                      else "")
+    if args.side == "none":
+        args.side = ""
     if args.gpus < 1:
         sys.exit("--gpus must be at least 1")
     world = os.environ.get("WORLD_SIZE")
