@@ -90,6 +90,10 @@ def _load():
     lib.oracle_clip_seeds.argtypes = [C.c_int, C.c_long, ip, dp, C.c_double, dp, dp]
     lib.oracle_energy_grad_clipped.argtypes = [np_, dp, dp, dp, ip, C.c_int, C.c_long, dp, dp, C.c_double, dp,
                                                dp]
+    lib.oracle_kfac_size.argtypes = [np_]
+    lib.oracle_kfac_size.restype = C.c_long
+    lib.oracle_kfac_factors.argtypes = [np_, dp, dp, dp, ip, C.c_long, dp, dp]
+    lib.oracle_kfac_precondition.argtypes = [np_, dp, dp, C.c_double, dp]
     lib.oracle_adapt_width.argtypes = [C.c_double] * 6
     lib.oracle_adapt_width.restype = C.c_double
     _lib = lib
@@ -245,6 +249,52 @@ def energy_grad_clipped(net, params, geoms, x, eloc, scale, geo=None):
     if rc:
         raise ValueError("oracle_energy_grad_clipped failed")
     return em, grad
+
+
+def kfac_factors(net, params, geoms, x, geo=None):
+    """Flat FP64 buffer of the KFAC factors (layout in ferminet_oracle.c)."""
+    lib = _load()
+    x = _d(x)
+    B = x.shape[0]
+    R, Z = _geo_arrays(geoms, net.n_nuc)
+    P = _d(params)
+    F = np.zeros(lib.oracle_kfac_size(C.byref(_net(net))))
+    g = _geo_idx(geo, B)
+    rc = lib.oracle_kfac_factors(C.byref(_net(net)), _dp(P), _dp(R), _dp(Z), g.ctypes.data_as(C.POINTER(C.c_int)),
+                                 B, _dp(x), _dp(F))
+    if rc:
+        raise ValueError("oracle_kfac_factors failed")
+    return F
+
+
+def kfac_precondition(net, factors, grad, lam):
+    lib = _load()
+    F = _d(factors)
+    gr = _d(grad)
+    out = np.zeros_like(gr)
+    if lib.oracle_kfac_precondition(C.byref(_net(net)), _dp(F), _dp(gr), float(lam), _dp(out)):
+        raise ValueError("oracle_kfac_precondition failed")
+    return out
+
+
+def kfac_blocks(net):
+    """Names, offsets and shapes of the factor blocks, in buffer order."""
+    L, d1, d2, K = net.n_layers, net.d1, net.d2, net.n_det
+    din1 = [4 * net.n_nuc if l == 0 else d1 for l in range(L)]
+    din2 = [4 if l == 0 else d2 for l in range(L)]
+    out, off = [], 0
+    for l in range(L):
+        a = 3 * din1[l] + 2 * din2[l] + 1
+        out.append((f"A1_{l}", off, a)); off += a * a
+        out.append((f"G1_{l}", off, d1)); off += d1 * d1
+    for l in range(L - 1):
+        a = din2[l] + 1
+        out.append((f"A2_{l}", off, a)); off += a * a
+        out.append((f"G2_{l}", off, d2)); off += d2 * d2
+    for s, ns in enumerate((net.n_up, net.n_down)):
+        out.append((f"Ao_{s}", off, d1 + 1)); off += (d1 + 1) ** 2
+        out.append((f"Go_{s}", off, K * ns)); off += (K * ns) ** 2
+    return out, off
 
 
 def adapt_width(width, accepted, moves, lo, hi, factor):

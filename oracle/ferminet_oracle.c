@@ -425,8 +425,22 @@ static void oracle_fwd(const onet* t, const olayout* Lo, const double* P, const 
 /* Reverse pass: seed * d log|psi| / d theta, accumulated into grad          */
 /* ------------------------------------------------------------------------ */
 
+/* Optional per-row accumulation of Kronecker factors during the reverse pass
+ * (KFAC; see oracle_kfac_factors).  Each matrix is summed, not averaged. */
+typedef struct {
+  double* A1[16]; double* G1[16];   /* one-electron layers: [wV+1]^2, [d1]^2   */
+  double* A2[16]; double* G2[16];   /* two-electron layers: [din2+1]^2, [d2]^2 */
+  double* Ao[2]; double* Go[2];     /* orbital blocks per spin: [d1+1]^2, [K n_s]^2 */
+} okfac;
+
+static void outer_acc(double* M, const double* u, int n) {
+  for (int a = 0; a < n; ++a)
+    if (u[a] != 0.0)
+      for (int b = 0; b < n; ++b) M[(size_t)a * n + b] += u[a] * u[b];
+}
+
 static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const double* R,
-                       const ofwd* f, double seed, double* G) {
+                       const ofwd* f, double seed, double* G, okfac* kf) {
   const int n = f->n, N = f->N, L = f->L, K = t->n_det, d1 = t->d1, d2 = t->d2;
   (void)R;
   if (f->sign == 0.0) return;
@@ -439,6 +453,9 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
     const double* w = P + Lo->w_orb[s];
     const double* pi = P + Lo->pi[s];
     const double* sg = P + Lo->sigma[s];
+    /* KFAC rows of the orbital layer: electron j's gradient over this spin's
+     * K n_s orbitals, and its input [h^L_j, 1] */
+    double* orow = kf ? calloc((size_t)ns * K * ns, sizeof(double)) : NULL;
     for (int k = 0; k < K; ++k) {
       double lk = f->ldet[2 * k] + f->ldet[2 * k + 1];
       double sk = f->sdet[2 * k] * f->sdet[2 * k + 1];
@@ -452,6 +469,7 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
           double ebar = Abar * f->orb[s][k * mat + i * ns + j];
           /* o = w_i . h_j + g_i */
           G[Lo->g_orb[s] + k * ns + i] += obar;
+          if (orow) orow[(size_t)j * K * ns + k * ns + i] = obar;
           for (int q = 0; q < d1; ++q) {
             G[Lo->w_orb[s] + ((size_t)k * ns + i) * d1 + q] += obar * f->h[L][(size_t)(j0 + j) * d1 + q];
             hbar[(size_t)(j0 + j) * d1 + q] += obar * w[((size_t)k * ns + i) * d1 + q];
@@ -484,6 +502,17 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
           }
         }
     }
+    if (orow) {
+      double* ab = malloc(sizeof(double) * (d1 + 1));
+      for (int j = 0; j < ns; ++j) {
+        outer_acc(kf->Go[s], orow + (size_t)j * K * ns, K * ns);
+        memcpy(ab, f->h[L] + (size_t)(j0 + j) * d1, sizeof(double) * d1);
+        ab[d1] = 1.0;
+        outer_acc(kf->Ao[s], ab, d1 + 1);
+      }
+      free(ab);
+      free(orow);
+    }
   }
   /* layers, last to first */
   double* ebar_next = NULL;  /* d/d e[l+1] */
@@ -493,11 +522,14 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
     /* two-electron layer l maps e[l] -> e[l+1] */
     if (l < L - 1) {
       const double* W = P + Lo->W[l];
-      for (int p = 0; p < n * n; ++p)
+      double* zrow = kf ? malloc(sizeof(double) * d2) : NULL;
+      double* arow = kf ? malloc(sizeof(double) * (a2 + 1)) : NULL;
+      for (int p = 0; p < n * n; ++p) {
         for (int o = 0; o < d2; ++o) {
           double eb = ebar_next[(size_t)p * d2 + o];
           double y = f->y2[l][(size_t)p * d2 + o];
           double zb = eb * (1.0 - y * y);
+          if (zrow) zrow[o] = zb;
           G[Lo->c[l] + o] += zb;
           for (int k = 0; k < a2; ++k) {
             G[Lo->W[l] + (size_t)o * a2 + k] += zb * f->e[l][(size_t)p * a2 + k];
@@ -505,13 +537,23 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
           }
           if (l >= 1) ebar[(size_t)p * a2 + o] += eb;
         }
+        if (kf) {
+          outer_acc(kf->G2[l], zrow, d2);
+          memcpy(arow, f->e[l] + (size_t)p * a2, sizeof(double) * a2);
+          arow[a2] = 1.0;
+          outer_acc(kf->A2[l], arow, a2 + 1);
+        }
+      }
+      free(zrow);
+      free(arow);
     }
     /* one-electron layer l maps h[l] -> h[l+1] */
     const double* V = P + Lo->V[l];
     double* hbar_prev = calloc((size_t)n * a1, sizeof(double));
     double* m1bar = calloc((size_t)2 * a1, sizeof(double));
     double* gbar = malloc(sizeof(double) * wV);
-    double* g = malloc(sizeof(double) * wV);
+    double* g = malloc(sizeof(double) * (wV + 1));
+    double* zrow = kf ? malloc(sizeof(double) * d1) : NULL;
     for (int i = 0; i < n; ++i) {
       memcpy(g, f->h[l] + (size_t)i * a1, sizeof(double) * a1);
       memcpy(g + a1, f->m1[l], sizeof(double) * 2 * a1);
@@ -521,12 +563,18 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
         double hb = hbar[(size_t)i * d1 + o];
         double y = f->y1[l][(size_t)i * d1 + o];
         double zb = hb * (1.0 - y * y);
+        if (zrow) zrow[o] = zb;
         G[Lo->b[l] + o] += zb;
         for (int k = 0; k < wV; ++k) {
           G[Lo->V[l] + (size_t)o * wV + k] += zb * g[k];
           gbar[k] += zb * V[(size_t)o * wV + k];
         }
         if (l >= 1) hbar_prev[(size_t)i * a1 + o] += hb;
+      }
+      if (kf) {  /* KFAC row: input [g_i, 1] and pre-activation gradient */
+        g[wV] = 1.0;
+        outer_acc(kf->A1[l], g, wV + 1);
+        outer_acc(kf->G1[l], zrow, d1);
       }
       for (int k = 0; k < a1; ++k) hbar_prev[(size_t)i * a1 + k] += gbar[k];
       for (int k = 0; k < 2 * a1; ++k) m1bar[k] += gbar[a1 + k];
@@ -541,7 +589,7 @@ static void oracle_bwd(const onet* t, const olayout* Lo, const double* P, const 
       int s = i < t->n_up ? 0 : 1;
       for (int k = 0; k < a1; ++k) hbar_prev[(size_t)i * a1 + k] += m1bar[s * a1 + k] / nspin(t, s);
     }
-    free(gbar); free(g); free(m1bar);
+    free(gbar); free(g); free(m1bar); free(zrow);
     free(hbar); hbar = hbar_prev;
     free(ebar_next); ebar_next = ebar;
   }
@@ -854,10 +902,225 @@ int oracle_logpsi_vjp(const onet* t, const double* P, const double* R, const dou
   for (long w = 0; w < B; ++w) {
     ofwd f;
     oracle_fwd(t, &Lo, P, R + (size_t)GEO(w) * 3 * N, x + (size_t)w * 3 * n, &f);
-    oracle_bwd(t, &Lo, P, R + (size_t)GEO(w) * 3 * N, &f, seeds[w], grad);
+    oracle_bwd(t, &Lo, P, R + (size_t)GEO(w) * 3 * N, &f, seeds[w], grad, NULL);
     fwd_free(&f);
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* KFAC (the optimiser the paper credits for FermiNet's accuracy, Sec. 1;    */
+/* Martens and Grosse 2015): Kronecker factors of the Fisher of log|psi|     */
+/* per layer, and the damped preconditioned update                           */
+/* ------------------------------------------------------------------------ */
+
+/* Factor buffer layout (doubles), in this order:
+ *   for each layer l: A1_l [wV+1]^2 (inputs [g_i, 1]), G1_l [d1]^2
+ *                     (pre-activation gradients of log|psi|);
+ *   for each l < L-1: A2_l [din2+1]^2 (inputs [e_ij, 1]), G2_l [d2]^2;
+ *   for each spin s:  Ao_s [d1+1]^2 (inputs [h^L_j, 1]), Go_s [K n_s]^2
+ *                     (gradients over the spin's K n_s orbitals);
+ *   D: the envelope parameters (pi and sigma blocks, in layout order), the
+ *      mean over walkers of the squared per-walker gradient (diagonal).
+ * Averages: A1 over B n rows, A2 over B n^2 rows, Ao_s over B n_s rows; every
+ * G and D over the B walkers (summed over a walker's rows). */
+typedef struct { long A1[16], G1[16], A2[16], G2[16], Ao[2], Go[2], D, total; } okfac_layout;
+
+static void kfac_layout(const onet* t, const olayout* Lo, okfac_layout* K) {
+  long off = 0;
+  const int L = t->n_layers;
+  for (int l = 0; l < L; ++l) {
+    const long a = 3L * din1_of(t, l) + 2L * din2_of(t, l) + 1;
+    K->A1[l] = off; off += a * a;
+    K->G1[l] = off; off += (long)t->d1 * t->d1;
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    const long a = din2_of(t, l) + 1;
+    K->A2[l] = off; off += a * a;
+    K->G2[l] = off; off += (long)t->d2 * t->d2;
+  }
+  for (int s = 0; s < 2; ++s) {
+    const long g = (long)t->n_det * nspin(t, s);
+    K->Ao[s] = off; off += (long)(t->d1 + 1) * (t->d1 + 1);
+    K->Go[s] = off; off += g * g;
+  }
+  K->D = off; off += Lo->total - Lo->pi[0];
+  K->total = off;
+}
+
+long oracle_kfac_size(const onet* t) {
+  if (check_net(t)) return -1;
+  olayout Lo; build_layout(t, &Lo, NULL, 0);
+  okfac_layout K; kfac_layout(t, &Lo, &K);
+  return K.total;
+}
+
+/* Kronecker factors over the batch (every walker on geometry geo[w]). */
+int oracle_kfac_factors(const onet* t, const double* P, const double* R, const double* Z, const int* geo, long B,
+                        const double* x, double* F) {
+  (void)Z;
+  if (check_net(t) || B < 1) return -1;
+  olayout Lo; build_layout(t, &Lo, NULL, 0);
+  okfac_layout KL; kfac_layout(t, &Lo, &KL);
+  const int n = t->n_up + t->n_down, N = t->n_nuc, L = t->n_layers;
+  memset(F, 0, sizeof(double) * KL.total);
+  okfac kf;
+  memset(&kf, 0, sizeof kf);
+  for (int l = 0; l < L; ++l) { kf.A1[l] = F + KL.A1[l]; kf.G1[l] = F + KL.G1[l]; }
+  for (int l = 0; l < L - 1; ++l) { kf.A2[l] = F + KL.A2[l]; kf.G2[l] = F + KL.G2[l]; }
+  for (int s = 0; s < 2; ++s) { kf.Ao[s] = F + KL.Ao[s]; kf.Go[s] = F + KL.Go[s]; }
+  const long ne = Lo.total - Lo.pi[0];
+  double* gw = malloc(sizeof(double) * Lo.total);
+  for (long w = 0; w < B; ++w) {
+    ofwd f;
+    oracle_fwd(t, &Lo, P, R + (size_t)GEO(w) * 3 * N, x + (size_t)w * 3 * n, &f);
+    memset(gw, 0, sizeof(double) * Lo.total);
+    oracle_bwd(t, &Lo, P, R + (size_t)GEO(w) * 3 * N, &f, 1.0, gw, &kf);
+    for (long k = 0; k < ne; ++k) F[KL.D + k] += gw[Lo.pi[0] + k] * gw[Lo.pi[0] + k];
+    fwd_free(&f);
+  }
+  free(gw);
+  /* averages */
+  for (int l = 0; l < L; ++l) {
+    const long a = 3L * din1_of(t, l) + 2L * din2_of(t, l) + 1;
+    for (long k = 0; k < a * a; ++k) F[KL.A1[l] + k] /= (double)B * n;
+    for (long k = 0; k < (long)t->d1 * t->d1; ++k) F[KL.G1[l] + k] /= (double)B;
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    const long a = din2_of(t, l) + 1;
+    for (long k = 0; k < a * a; ++k) F[KL.A2[l] + k] /= (double)B * n * n;
+    for (long k = 0; k < (long)t->d2 * t->d2; ++k) F[KL.G2[l] + k] /= (double)B;
+  }
+  for (int s = 0; s < 2; ++s) {
+    const long g = (long)t->n_det * nspin(t, s);
+    for (long k = 0; k < (long)(t->d1 + 1) * (t->d1 + 1); ++k)
+      F[KL.Ao[s] + k] = nspin(t, s) ? F[KL.Ao[s] + k] / ((double)B * nspin(t, s)) : 0.0;
+    for (long k = 0; k < g * g; ++k) F[KL.Go[s] + k] /= (double)B;
+  }
+  for (long k = 0; k < ne; ++k) F[KL.D + k] /= (double)B;
+  return 0;
+}
+
+/* Inverse of a symmetric positive definite n x n matrix by Gauss-Jordan
+ * elimination (row pivoting kept for safety). */
+static int gj_inverse(int n, const double* M, double* inv) {
+  double* a = malloc(sizeof(double) * (size_t)n * n);
+  memcpy(a, M, sizeof(double) * (size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) inv[(size_t)i * n + j] = i == j ? 1.0 : 0.0;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i) if (fabs(a[(size_t)i * n + k]) > fabs(a[(size_t)p * n + k])) p = i;
+    if (a[(size_t)p * n + k] == 0.0) { free(a); return -1; }
+    if (p != k)
+      for (int j = 0; j < n; ++j) {
+        double u = a[(size_t)k * n + j]; a[(size_t)k * n + j] = a[(size_t)p * n + j]; a[(size_t)p * n + j] = u;
+        u = inv[(size_t)k * n + j]; inv[(size_t)k * n + j] = inv[(size_t)p * n + j]; inv[(size_t)p * n + j] = u;
+      }
+    const double piv = a[(size_t)k * n + k];
+    for (int j = 0; j < n; ++j) { a[(size_t)k * n + j] /= piv; inv[(size_t)k * n + j] /= piv; }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double fct = a[(size_t)i * n + k];
+      if (fct == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        a[(size_t)i * n + j] -= fct * a[(size_t)k * n + j];
+        inv[(size_t)i * n + j] -= fct * inv[(size_t)k * n + j];
+      }
+    }
+  }
+  free(a);
+  return 0;
+}
+
+/* Delta = (G + gamma I)^-1 M (A + gamma I)^-1 for M [g][a]. */
+static int kfac_block(int g, int a, const double* G, const double* A, double gamma, const double* M, double* out) {
+  double* Gi = malloc(sizeof(double) * (size_t)g * g);
+  double* Ai = malloc(sizeof(double) * (size_t)a * a);
+  double* Gd = malloc(sizeof(double) * (size_t)g * g);
+  double* Ad = malloc(sizeof(double) * (size_t)a * a);
+  double* X = calloc((size_t)g * a, sizeof(double));
+  memcpy(Gd, G, sizeof(double) * (size_t)g * g);
+  memcpy(Ad, A, sizeof(double) * (size_t)a * a);
+  for (int i = 0; i < g; ++i) Gd[(size_t)i * g + i] += gamma;
+  for (int i = 0; i < a; ++i) Ad[(size_t)i * a + i] += gamma;
+  int rc = gj_inverse(g, Gd, Gi) | gj_inverse(a, Ad, Ai);
+  if (!rc) {
+    for (int i = 0; i < g; ++i)
+      for (int k = 0; k < g; ++k) {
+        const double c = Gi[(size_t)i * g + k];
+        for (int j = 0; j < a; ++j) X[(size_t)i * a + j] += c * M[(size_t)k * a + j];
+      }
+    for (int i = 0; i < g; ++i)
+      for (int j = 0; j < a; ++j) {
+        double v = 0.0;
+        for (int k = 0; k < a; ++k) v += X[(size_t)i * a + k] * Ai[(size_t)k * a + j];
+        out[(size_t)i * a + j] = v;
+      }
+  }
+  free(Gi); free(Ai); free(Gd); free(Ad); free(X);
+  return rc;
+}
+
+/* KFAC-preconditioned update of a gradient over the whole parameter vector:
+ * for each layer block (weights and bias together as M = [W b]),
+ * Delta = (G + sqrt(lambda) I)^-1 M (A + sqrt(lambda) I)^-1; envelope entries
+ * grad / (D + lambda). */
+int oracle_kfac_precondition(const onet* t, const double* F, const double* grad, double lambda, double* out) {
+  if (check_net(t) || !(lambda > 0)) return -1;
+  olayout Lo; build_layout(t, &Lo, NULL, 0);
+  okfac_layout KL; kfac_layout(t, &Lo, &KL);
+  const int L = t->n_layers, d1 = t->d1, d2 = t->d2;
+  const double gamma = sqrt(lambda);
+  int rc = 0;
+  for (int l = 0; l < L; ++l) {
+    const int wV = 3 * din1_of(t, l) + 2 * din2_of(t, l), a = wV + 1;
+    double* M = malloc(sizeof(double) * (size_t)d1 * a);
+    double* D = malloc(sizeof(double) * (size_t)d1 * a);
+    for (int o = 0; o < d1; ++o) {
+      for (int k = 0; k < wV; ++k) M[(size_t)o * a + k] = grad[Lo.V[l] + (size_t)o * wV + k];
+      M[(size_t)o * a + wV] = grad[Lo.b[l] + o];
+    }
+    rc |= kfac_block(d1, a, F + KL.G1[l], F + KL.A1[l], gamma, M, D);
+    for (int o = 0; o < d1; ++o) {
+      for (int k = 0; k < wV; ++k) out[Lo.V[l] + (size_t)o * wV + k] = D[(size_t)o * a + k];
+      out[Lo.b[l] + o] = D[(size_t)o * a + wV];
+    }
+    free(M); free(D);
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    const int a2 = din2_of(t, l), a = a2 + 1;
+    double* M = malloc(sizeof(double) * (size_t)d2 * a);
+    double* D = malloc(sizeof(double) * (size_t)d2 * a);
+    for (int o = 0; o < d2; ++o) {
+      for (int k = 0; k < a2; ++k) M[(size_t)o * a + k] = grad[Lo.W[l] + (size_t)o * a2 + k];
+      M[(size_t)o * a + a2] = grad[Lo.c[l] + o];
+    }
+    rc |= kfac_block(d2, a, F + KL.G2[l], F + KL.A2[l], gamma, M, D);
+    for (int o = 0; o < d2; ++o) {
+      for (int k = 0; k < a2; ++k) out[Lo.W[l] + (size_t)o * a2 + k] = D[(size_t)o * a + k];
+      out[Lo.c[l] + o] = D[(size_t)o * a + a2];
+    }
+    free(M); free(D);
+  }
+  for (int s = 0; s < 2; ++s) {
+    const int g = t->n_det * nspin(t, s), a = d1 + 1;
+    if (g == 0) continue;
+    double* M = malloc(sizeof(double) * (size_t)g * a);
+    double* D = malloc(sizeof(double) * (size_t)g * a);
+    for (int q = 0; q < g; ++q) {
+      for (int f = 0; f < d1; ++f) M[(size_t)q * a + f] = grad[Lo.w_orb[s] + (size_t)q * d1 + f];
+      M[(size_t)q * a + d1] = grad[Lo.g_orb[s] + q];
+    }
+    rc |= kfac_block(g, a, F + KL.Go[s], F + KL.Ao[s], gamma, M, D);
+    for (int q = 0; q < g; ++q) {
+      for (int f = 0; f < d1; ++f) out[Lo.w_orb[s] + (size_t)q * d1 + f] = D[(size_t)q * a + f];
+      out[Lo.g_orb[s] + q] = D[(size_t)q * a + d1];
+    }
+    free(M); free(D);
+  }
+  for (long k = 0; k < Lo.total - Lo.pi[0]; ++k) out[Lo.pi[0] + k] = grad[Lo.pi[0] + k] / (F[KL.D + k] + lambda);
+  return rc ? -1 : 0;
 }
 
 /* VMC energy gradient (Eq. 2 differentiated with E_L held fixed): per

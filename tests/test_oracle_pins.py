@@ -542,3 +542,94 @@ def test_full_covariance_derivatives_and_parameter_gradient_by_differences():
         lpm, _ = oracle.logpsi(net, P - eps * v, [geom], x)
         fd = seeds @ ((lpp - lpm) / (2 * eps))
         assert abs(fd - g @ v) < 2e-6 * max(1.0, abs(fd)), e.name
+
+
+# ---------------------------------------------------------------------------
+# KFAC factors and preconditioner (Sec. 1: the optimiser behind FermiNet)
+# ---------------------------------------------------------------------------
+
+def _kfac_block(net, F, name):
+    blocks, _ = oracle.kfac_blocks(net)
+    _, off, d = next(b for b in blocks if b[0] == name)
+    return F[off:off + d * d].reshape(d, d)
+
+
+def test_kfac_single_row_factors_are_rank_one_gradient_pieces():
+    """One walker with one electron: every one-electron layer and the orbital
+    layer see a single row, so A = a a^T and G = d d^T with grad = d a^T
+    ([W b] of the reverse pass, seed 1): grad grad^T = tr(A) G and
+    grad^T grad = tr(G) A."""
+    net = synth.Net(3, 10, 6, 3, 1, 0, 2)
+    lay, P = _params(net, 51)
+    rng = np.random.default_rng(52)
+    for e in lay:
+        if e.name.startswith(("b", "g_orb", "pi_", "sigma_")):
+            P[e.offset:e.offset + e.count] = 0.3 + rng.random(e.count)
+    geom = synth.Geometry(R=np.array([[0.0, 0.0, 0.0], [0.4, 1.1, -0.2]]), Z=np.array([1.0, 1.0]))
+    x = rng.standard_normal((1, 1, 3))
+    F = oracle.kfac_factors(net, P, [geom], x)
+    g = oracle.logpsi_vjp(net, P, [geom], x, np.ones(1))
+    for l in range(net.n_layers):
+        wV = 3 * (4 * net.n_nuc if l == 0 else net.d1) + 2 * (4 if l == 0 else net.d2)
+        W = np.concatenate([_block(lay, g, f"V{l}").reshape(net.d1, wV), _block(lay, g, f"b{l}")[:, None]], axis=1)
+        A, G = _kfac_block(net, F, f"A1_{l}"), _kfac_block(net, F, f"G1_{l}")
+        np.testing.assert_allclose(W @ W.T, np.trace(A) * G, rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(W.T @ W, np.trace(G) * A, rtol=1e-10, atol=1e-12)
+    W = np.concatenate([_block(lay, g, "w_orb_up").reshape(-1, net.d1), _block(lay, g, "g_orb_up")[:, None]], axis=1)
+    A, G = _kfac_block(net, F, "Ao_0"), _kfac_block(net, F, "Go_0")
+    np.testing.assert_allclose(W @ W.T, np.trace(A) * G, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(W.T @ W, np.trace(G) * A, rtol=1e-10, atol=1e-12)
+
+
+def test_kfac_envelope_diagonal_and_batch_averaging():
+    """D is the mean squared per-walker gradient of the envelope parameters
+    (against per-walker reverse passes), and every factor of a batch is the
+    walker-weighted mean of the factors of its parts."""
+    net = synth.Net(2, 8, 4, 2, 2, 1, 2)
+    lay, P = _params(net, 53)
+    geom = synth.Geometry(R=np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 1.3]]), Z=np.array([2.0, 1.0]))
+    x = np.random.default_rng(54).standard_normal((5, 3, 3))
+    F = oracle.kfac_factors(net, P, [geom], x)
+    _, nb = oracle.kfac_blocks(net)
+    p0 = next(e.offset for e in lay if e.name == "pi_up")
+    gw = np.stack([oracle.logpsi_vjp(net, P, [geom], x, np.eye(5)[w]) for w in range(5)])
+    np.testing.assert_allclose(F[nb:], (gw[:, p0:] ** 2).mean(axis=0), rtol=1e-10, atol=1e-14)
+    F1 = oracle.kfac_factors(net, P, [geom], x[:2])
+    F2 = oracle.kfac_factors(net, P, [geom], x[2:])
+    np.testing.assert_allclose(F, (2 * F1 + 3 * F2) / 5, rtol=1e-10, atol=1e-14)
+    for name, off, d in oracle.kfac_blocks(net)[0]:  # symmetric positive semidefinite
+        M = F[off:off + d * d].reshape(d, d)
+        np.testing.assert_allclose(M, M.T, rtol=0, atol=1e-12 * max(1.0, np.abs(M).max()))
+        assert np.linalg.eigvalsh(M).min() > -1e-10 * max(1.0, np.abs(M).max()), name
+
+
+def test_kfac_precondition_against_library_solves():
+    """Each layer block of the update is (G + sqrt(l) I)^-1 [W b] (A + sqrt(l) I)^-1
+    (checked against numpy's dense solves), envelope entries grad / (D + l), and
+    a huge damping reduces the update to grad / l."""
+    net = synth.Net(2, 8, 4, 2, 2, 1, 2)
+    lay, P = _params(net, 55)
+    geom = synth.Geometry(R=np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 1.3]]), Z=np.array([2.0, 1.0]))
+    x = np.random.default_rng(56).standard_normal((4, 3, 3))
+    F = oracle.kfac_factors(net, P, [geom], x)
+    grad = np.random.default_rng(57).standard_normal(P.shape[0])
+    lam = 1e-2
+    out = oracle.kfac_precondition(net, F, grad, lam)
+    g = np.sqrt(lam)
+    for l in range(net.n_layers):
+        wV = 3 * (4 * net.n_nuc if l == 0 else net.d1) + 2 * (4 if l == 0 else net.d2)
+        M = np.concatenate([_block(lay, grad, f"V{l}").reshape(net.d1, wV), _block(lay, grad, f"b{l}")[:, None]], 1)
+        A, G = _kfac_block(net, F, f"A1_{l}"), _kfac_block(net, F, f"G1_{l}")
+        want = np.linalg.solve(G + g * np.eye(len(G)), M) @ np.linalg.inv(A + g * np.eye(len(A)))
+        got = np.concatenate([_block(lay, out, f"V{l}").reshape(net.d1, wV), _block(lay, out, f"b{l}")[:, None]], 1)
+        np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-10 * np.abs(want).max())
+    M = np.concatenate([_block(lay, grad, "w_orb_down").reshape(-1, net.d1), _block(lay, grad, "g_orb_down")[:, None]], 1)
+    A, G = _kfac_block(net, F, "Ao_1"), _kfac_block(net, F, "Go_1")
+    want = np.linalg.solve(G + g * np.eye(len(G)), M) @ np.linalg.inv(A + g * np.eye(len(A)))
+    got = np.concatenate([_block(lay, out, "w_orb_down").reshape(-1, net.d1), _block(lay, out, "g_orb_down")[:, None]], 1)
+    np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-10 * np.abs(want).max())
+    _, nb = oracle.kfac_blocks(net)
+    p0 = next(e.offset for e in lay if e.name == "pi_up")
+    np.testing.assert_allclose(out[p0:], grad[p0:] / (F[nb:] + lam), rtol=1e-12)
+    big = oracle.kfac_precondition(net, F, grad, 1e16)
+    np.testing.assert_allclose(big * 1e16, grad, rtol=1e-4, atol=1e-6 * np.abs(grad).max())
