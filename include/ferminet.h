@@ -223,6 +223,36 @@ typedef struct {
 } fn_train_opts;
 fn_status ferminet_set_train_opts(fn_ctx* ctx, const fn_train_opts* opts);
 
+/* KFAC, the second-order optimiser the paper credits for FermiNet's accuracy
+ * (Sec. 1; Martens and Grosse 2015).  The paper gives no detail; the reading:
+ * Kronecker factors of the Fisher of log|psi| for every dense layer.
+ *   ferminet_kfac_size: length of the factor buffer in doubles.  Layout: for
+ *     each layer l, A1_l [wV+1]^2 (one-electron inputs [h_i, mean_up h,
+ *     mean_down h, mean_up h_i., mean_down h_i., 1], wV = 3 a + 2 e) and
+ *     G1_l [d1]^2 (gradients of log|psi| with respect to the pre-activations);
+ *     for each l < L-1, A2_l [e+1]^2 (pair inputs [h_ij, 1]) and G2_l [d2]^2;
+ *     for each spin, Ao [d1+1]^2 (inputs [h^L_j, 1] of that spin's electrons)
+ *     and Go [K n_s]^2 (gradients over that spin's orbitals); then D, one
+ *     entry per envelope parameter (pi and sigma blocks in layout order).
+ *     Every A is averaged over its rows (B n, B n^2, B n_s), every G and D
+ *     over the B walkers; D is the mean squared per-walker gradient.
+ *   ferminet_kfac_factors: fills d_factors (device, FP64) for the batch d_x.
+ *     Mixed-precision contexts only (FN_EINVAL otherwise): it runs the
+ *     tensor-core adjoint with unit seeds and forms the factors as tensor-core
+ *     Gram products of the stored rows (two-electron factors: FP32 SIMT).
+ *     Synchronises the stream.
+ *   ferminet_kfac_precondition: d_out [n_params] (float) = the update for the
+ *     gradient d_grad [n_params]: for each layer, with M = [W b] its gradient,
+ *     (G + sqrt(lambda) I)^-1 M (A + sqrt(lambda) I)^-1 (orbital layers per
+ *     spin, weights and biases of the K n_s orbitals); envelope entries
+ *     grad / (D + lambda).  The damped factors are inverted in FP64 on the
+ *     device (Gauss-Jordan, one launch per pivot step, every factor at once);
+ *     the products run in FP32.  lambda > 0.  Synchronises the stream. */
+fn_status ferminet_kfac_size(const fn_net* net, long* n_doubles);
+fn_status ferminet_kfac_factors(fn_ctx* ctx, const float* d_x, long B, double* d_factors);
+fn_status ferminet_kfac_precondition(fn_ctx* ctx, const double* d_factors, const float* d_grad, float lambda,
+                                     float* d_out);
+
 /* n_steps Gaussian all-electron Metropolis moves sampling |psi|^2 (Eq. 2).
  * Step s uses counter t = counter + s.  For walker w the proposal is
  * x' = x + width * z with z drawn by Philox4x32-10 (key {seed lo, seed hi},

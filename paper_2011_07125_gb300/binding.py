@@ -67,7 +67,8 @@ EXPORTS = ("ferminet_init", "ferminet_param_layout", "ferminet_net_layout", "fer
            "ferminet_logpsi", "ferminet_local_energy", "ferminet_logpsi_vjp", "ferminet_energy_grad",
            "ferminet_energy_sums", "ferminet_energy_grad_partial", "ferminet_mcmc_step", "ferminet_step", "ferminet_sync", "ferminet_flagged_matrices", "ferminet_profile",
            "ferminet_profile_read", "ferminet_launch_count", "ferminet_get_tuning", "ferminet_set_tuning",
-           "ferminet_autotune", "ferminet_set_train_opts", "ferminet_last_error", "ferminet_destroy")
+           "ferminet_autotune", "ferminet_set_train_opts", "ferminet_kfac_size", "ferminet_kfac_factors",
+           "ferminet_kfac_precondition", "ferminet_last_error", "ferminet_destroy")
 KERNEL_CLASSES = {"tangent_gemm": 0, "det_tangent": 1, "two_layer": 2, "means": 3, "tanh": 4, "value_pass": 5,
                   "adjoint": 6}
 
@@ -115,6 +116,9 @@ def load(path: Optional[str] = None):
         lib.ferminet_set_tuning.argtypes = [vp, C.POINTER(FnTuning)]
         lib.ferminet_autotune.argtypes = [vp, vp, C.c_long, C.c_int, C.POINTER(FnTuning)]
         lib.ferminet_set_train_opts.argtypes = [vp, C.POINTER(FnTrainOpts)]
+        lib.ferminet_kfac_size.argtypes = [C.POINTER(FnNet), C.POINTER(C.c_long)]
+        lib.ferminet_kfac_factors.argtypes = [vp, vp, C.c_long, vp]
+        lib.ferminet_kfac_precondition.argtypes = [vp, vp, vp, C.c_float, vp]
         lib.ferminet_launch_count.argtypes = []
         lib.ferminet_launch_count.restype = C.c_longlong
         for f in EXPORTS:
@@ -383,6 +387,31 @@ class FermiNet:
         o = FnTrainOpts(float(clip_scale), None if width is None else width.data_ptr(), float(accept_lo),
                         float(accept_hi), float(width_factor))
         self._check(self.lib.ferminet_set_train_opts(self.ctx, C.byref(o)), "ferminet_set_train_opts")
+
+    def kfac_size(self):
+        n = C.c_long(0)
+        fnet = _net(self.net)
+        self._check(self.lib.ferminet_kfac_size(C.byref(fnet), C.byref(n)), "ferminet_kfac_size")
+        return int(n.value)
+
+    def kfac_factors(self, x):
+        """KFAC factors of the batch (float64 CUDA tensor; layout in ferminet.h)."""
+        B = x.shape[0]
+        self._f32(x, (B, self.n, 3))
+        F = self._empty(self.kfac_size(), dtype=self.torch.float64)
+        self._check(self.lib.ferminet_kfac_factors(self.ctx, _ptr(x), B, _ptr(F)), "ferminet_kfac_factors")
+        return F
+
+    def kfac_precondition(self, factors, grad, lam):
+        """KFAC update for a gradient (float32 [n_params])."""
+        torch = self.torch
+        if not (factors.is_cuda and factors.dtype == torch.float64 and factors.is_contiguous()):
+            raise FermiNetError("expected a contiguous float64 CUDA factor buffer")
+        self._f32(grad, (self.n_params,))
+        out = self._empty(self.n_params)
+        self._check(self.lib.ferminet_kfac_precondition(self.ctx, _ptr(factors), _ptr(grad), float(lam), _ptr(out)),
+                    "ferminet_kfac_precondition")
+        return out
 
     def flagged_matrices(self):
         return int(self.lib.ferminet_flagged_matrices(self.ctx))

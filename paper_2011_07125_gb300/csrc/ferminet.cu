@@ -672,8 +672,55 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
 }
 
 // ---------------------------------------------------------------------------
+// KFAC factor buffer (the same layout as the oracle's): per one-electron layer
+// A1 [wV+1]^2, G1 [d1]^2; per two-electron layer A2 [din2+1]^2, G2 [d2]^2; per
+// spin Ao [d1+1]^2, Go [K n_s]^2; then the envelope diagonal D.
+struct KfacLayout {
+  long A1[16] = {}, G1[16] = {}, A2[16] = {}, G2[16] = {}, Ao[2] = {}, Go[2] = {}, D = 0, total = 0;
+  long dA1[16] = {}, dA2[16] = {}, dGo[2] = {};
+};
+
+void kfac_layout(const fn_net& t, const Layout& lay, KfacLayout* K) {
+  long off = 0;
+  for (int l = 0; l < t.n_layers; ++l) {
+    K->dA1[l] = 3L * din1_of(t, l) + 2L * din2_of(t, l) + 1;
+    K->A1[l] = off;
+    off += K->dA1[l] * K->dA1[l];
+    K->G1[l] = off;
+    off += (long)t.d1 * t.d1;
+  }
+  for (int l = 0; l < t.n_layers - 1; ++l) {
+    K->dA2[l] = din2_of(t, l) + 1;
+    K->A2[l] = off;
+    off += K->dA2[l] * K->dA2[l];
+    K->G2[l] = off;
+    off += (long)t.d2 * t.d2;
+  }
+  for (int s = 0; s < 2; ++s) {
+    K->dGo[s] = (long)t.n_det * (s == 0 ? t.n_up : t.n_down);
+    K->Ao[s] = off;
+    off += (long)(t.d1 + 1) * (t.d1 + 1);
+    K->Go[s] = off;
+    off += K->dGo[s] * K->dGo[s];
+  }
+  K->D = off;
+  off += lay.total - lay.pi[0];
+  K->total = off;
+}
+
+// Factor accumulation during an adjoint with unit seeds.
+struct KfacAcc {
+  double* F;
+  KfacLayout L;
+};
+
+// ---------------------------------------------------------------------------
 // Tensor-core contractions of the adjoint (BF16 hi + lo operands, FP32
 // accumulation in TMEM).
+
+inline void fail_if_gram(fn_ctx* c, bool ok) {
+  if (!ok) c->host_fail = true;
+}
 
 // Split count of a weight-gradient contraction: about two waves of tiles.
 int tn_ksplit(long Pn, long Qn, long K) {
@@ -761,7 +808,8 @@ bool tc_nn(fn_ctx* c, cudaStream_t s, long rows, long Nn, long K, __nv_bfloat16*
 // with an FP64 reduction) and backward-data products (transposed weights) --
 // runs on tcgen05.  Elementwise steps, the determinant adjoint and the
 // two-electron backward are those of the FP32 schedule.
-void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const float* seeds, double* grad) {
+void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const float* seeds, double* grad,
+                  const KfacAcc* kf = nullptr) {
   const fn_net& t = c->net;
   const int n = c->n, N = c->N, L = t.n_layers, K = t.n_det, d1 = t.d1, d2 = t.d2;
   const long Ktot = (long)K * n, rows = Bc * n, pairs = Bc * n * n;
@@ -806,13 +854,34 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
     cs_need(pairs, d2);
     tn_max = std::max(tn_max, (long)gemm_tn_splits(d2, a2, pairs) * d2 * a2);
   }
+  // KFAC: transposed input rows of the factor Grams, more split-K partials,
+  // and the two-electron gradients materialised (separate backward kernels)
+  __nv_bfloat16* TK[2] = {};
+  if (kf) {
+    long tk_rows = t.d1 + 1;
+    for (int l = 0; l < L; ++l) {
+      tk_rows = std::max(tk_rows, kf->L.dA1[l]);
+      part_need(kf->L.dA1[l], kf->L.dA1[l], ldk);
+      tn_max = std::max(tn_max, (long)gemm_tn_splits(din2_of(t, l), din2_of(t, l), pairs) * din2_of(t, l) *
+                                    din2_of(t, l));
+      tn_max = std::max(tn_max, (long)gemm_tn_splits(d2, d2, pairs) * d2 * d2);
+      cs_need(pairs, din2_of(t, l));
+    }
+    part_need(d1, d1, ldk);
+    part_need(t.d1 + 1, t.d1 + 1, ldk);
+    for (int sp = 0; sp < 2; ++sp) part_need(kf->L.dGo[sp], kf->L.dGo[sp], ldk);
+    for (int h = 0; h < (two ? 2 : 1); ++h) TK[h] = ar.get<__nv_bfloat16>(tk_rows * ldk);
+  }
   float* part = ar.get<float>(part_max);
   double* cs_scr = ar.get<double>(cs_max);
-  bool pair_bwd = c->tune.pair_unfused == 0;
+  bool pair_bwd = c->tune.pair_unfused == 0 && !kf;
   for (int l = 0; l < L - 1 && pair_bwd; ++l) pair_bwd = pair_bwd_supported(din2_of(t, l), d2);
   float* pb_scr = pair_bwd ? ar.get<float>(pair_bwd_scratch_floats(d2, d2)) : nullptr;
   float* tn_scr = pair_bwd ? nullptr : ar.get<float>(tn_max);
   if (ar.measure) return;
+  auto gram = [&](long dim, __nv_bfloat16* const rows_t[2], long ldr, double* dst) {
+    if (dim > 0) fail_if_gram(c, tc_tn(c, c->stream, dim, dim, ldr, rows_t, rows_t, dst, dim, part));
+  };
 
   cudaStream_t s = c->stream;
   const float* P = c->d_params;
@@ -845,10 +914,30 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
   ad.envgrad = envg;
   launch_adj_det(s, ad);
   launch_colsum_accum(s, envg, Bc, env_cols, env_cols, grad + Lo.pi[0], cs_scr);
+  if (kf) launch_colsq_accum(s, envg, Bc, env_cols, env_cols, kf->F + kf->L.D);
   // orbital weights: grad[q][f] += sum_r Obar[r][q] h^L[r][f]
   launch_t_bf16(s, st.Hb[L][0], st.Hb[L][1], ldh, rows, d1, TA[0], TA[1], ldk);
   launch_t_split(s, Obar, Ktot, rows, Ktot, TB[0], TB[1], ldk);
   fail_if(tc_tn(c, s, Ktot, d1, ldk, TA, TB, grad + Lo.w_orb, d1, part));
+  if (kf) {  // orbital factors per spin: gradient rows over the spin's orbitals, inputs [h^L, 1]
+    for (int sp = 0; sp < 2; ++sp) {
+      const int nsp = sp == 0 ? t.n_up : t.n_down;
+      if (nsp == 0) continue;
+      const long q0 = sp == 0 ? 0 : (long)K * t.n_up;
+      __nv_bfloat16* const gq[2] = {TB[0] + q0 * ldk, two ? TB[1] + q0 * ldk : nullptr};
+      gram(kf->L.dGo[sp], gq, ldk, kf->F + kf->L.Go[sp]);
+      KfacRows kr{};
+      kr.seg[0] = {st.Hb[L][0], st.Hb[L][1], ldh, 0, d1, 1};
+      kr.nseg = 1;
+      kr.rows = rows;
+      kr.cols = d1 + 1;
+      kr.spin = sp;
+      kr.n = n;
+      kr.n_up = t.n_up;
+      launch_kfac_rows(s, kr, TK[0], TK[1], ldk);
+      gram(d1 + 1, TK, ldk, kf->F + kf->L.Ao[sp]);
+    }
+  }
   launch_colsum_accum(s, Obar, rows, Ktot, Ktot, grad + Lo.g_orb, cs_scr);
   // h^L gradient: Obar W_orb
   launch_split_bf16(s, Obar, Ktot, rows, Ktot, Xs[0], Xs[1], lko);
@@ -879,6 +968,13 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
       launch_tanh_bwd(s, Enext, st.Y2[l], pairs, d2, Z2bar);
       gemm_tn_accum(s, d2, a2, pairs, Z2bar, d2, st.E[l], a2, grad + Lo.W[l], a2, tn_scr,
                     gemm_tn_splits(d2, a2, pairs));
+      if (kf) {  // two-electron factors (FP32 SIMT Grams over the pair rows, FP64 sums)
+        gemm_tn_accum(s, d2, d2, pairs, Z2bar, d2, Z2bar, d2, kf->F + kf->L.G2[l], d2, tn_scr,
+                      gemm_tn_splits(d2, d2, pairs));
+        gemm_tn_accum(s, a2, a2, pairs, st.E[l], a2, st.E[l], a2, kf->F + kf->L.A2[l], a2 + 1, tn_scr,
+                      gemm_tn_splits(a2, a2, pairs));
+        launch_colsum_accum(s, st.E[l], pairs, a2, a2, kf->F + kf->L.A2[l] + (long)a2 * (a2 + 1), cs_scr);
+      }
       launch_colsum_accum(s, Z2bar, pairs, d2, d2, grad + Lo.c[l], cs_scr);
       gemm_nn(s, pairs, a2, d2, Z2bar, d2, P + Lo.W[l], a2, Ecur, a2, Epi{});
       if (l >= 1) launch_add(s, Ecur, Enext, pairs * a2);
@@ -891,6 +987,21 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
     launch_t_bf16(s, st.Hb[l][0], st.Hb[l][1], l == 0 ? ldh0 : ldh, rows, a1, TA[0], TA[1], ldk);
     launch_t_split(s, Zbar, d1, rows, d1, TB[0], TB[1], ldk);
     fail_if(tc_tn(c, s, d1, a1, ldk, TA, TB, grad + Lo.V[l], wV, part));
+    if (kf) {  // one-electron factors: pre-activation gradients and inputs [h, m_up, m_down, m2_up, m2_down, 1]
+      gram(d1, TB, ldk, kf->F + kf->L.G1[l]);
+      KfacRows kr{};
+      kr.seg[0] = {st.Hb[l][0], st.Hb[l][1], l == 0 ? ldh0 : ldh, 0, a1, 1};
+      kr.seg[1] = {st.M1b[l][0], st.M1b[l][1], pad64(2 * a1), a1, 2 * a1, n};
+      kr.seg[2] = {st.M2b[l][0], st.M2b[l][1], pad64(2 * a2), 3 * a1, 2 * a2, 1};
+      kr.nseg = 3;
+      kr.rows = rows;
+      kr.cols = wV + 1;
+      kr.spin = -1;
+      kr.n = n;
+      kr.n_up = t.n_up;
+      launch_kfac_rows(s, kr, TK[0], TK[1], ldk);
+      gram(wV + 1, TK, ldk, kf->F + kf->L.A1[l]);
+    }
     // V_de: the pair means
     launch_t_bf16(s, st.M2b[l][0], st.M2b[l][1], pad64(2 * a2), rows, 2 * a2, TA[0], TA[1], ldk);
     fail_if(tc_tn(c, s, d1, 2 * a2, ldk, TA, TB, grad + Lo.V[l] + 3 * a1, wV, part));
@@ -1065,6 +1176,11 @@ size_t ws_bytes(fn_ctx* c, long Bc, int mode) {
   if (mode == 0) forward(c, ar, nullptr, Bc, 0, false, false, FwdOut{}, nullptr);
   if (mode == 1) forward(c, ar, nullptr, Bc, 0, true, false, FwdOut{}, nullptr);
   if (mode == 2) vjp_chunk(c, ar, nullptr, Bc, 0, nullptr, nullptr);
+  if (mode == 3) {  // KFAC factors: the tensor-core adjoint with the factor Grams
+    KfacAcc kf{};
+    kfac_layout(c->net, c->lay, &kf.L);
+    vjp_chunk_tc(c, ar, nullptr, Bc, 0, nullptr, nullptr, &kf);
+  }
   return ar.off;
 }
 
@@ -1201,6 +1317,68 @@ fn_status run_vjp(fn_ctx* c, const float* x, long B, const float* seeds, float* 
     }
   }
   if (grad) launch_d2f(s, grad64, grad, c->lay.total);
+  return after_launch(c);
+}
+
+// KFAC factor sums over the batch (unit seeds), then their averages.
+fn_status run_kfac(fn_ctx* c, const float* x, long B, double* F) {
+  cudaStream_t s = c->stream;
+  KfacAcc kf{};
+  kf.F = F;
+  kfac_layout(c->net, c->lay, &kf.L);
+  launch_zero_d(s, F, kf.L.total);
+  const long ch = chunk_for(c, B, 3);
+  fn_status st = ensure_ws(c, ws_bytes(c, ch, 3));
+  if (st != FN_OK) return st;
+  st = ensure_aux(c, std::max<long>(B, 1));
+  if (st != FN_OK) return st;
+  float* ones = c->aux;
+  launch_fill(s, ones, 1.f, B);
+  launch_zero_d(s, c->d_grad64, c->lay.total);
+  const long n3 = 3L * c->n;
+  for (long w0 = 0; w0 < B; w0 += ch) {
+    const long Bc = std::min(ch, B - w0);
+    Arena ar;
+    ar.measure = false;
+    ar.base = c->ws;
+    vjp_chunk_tc(c, ar, x + w0 * n3, Bc, w0, ones + w0, c->d_grad64, &kf);
+  }
+  if (c->host_fail) {
+    c->host_fail = false;
+    return fail(c, FN_ECUDA, "tensor-core GEMM set-up failed (tensor map or launch)");
+  }
+  // averages: inputs over rows, gradients and the envelope diagonal over walkers
+  const fn_net& t = c->net;
+  const double Bd = (double)B, n = (double)c->n;
+  std::vector<KfacBlock> blk;
+  auto add = [&](long off, long dim, int diag, double scale, int mirror, double count) {
+    KfacBlock b{};
+    b.off = off;
+    b.dim = dim;
+    b.diag = diag;
+    b.scale = scale;
+    b.mirror_bias = mirror;
+    b.count = count;
+    blk.push_back(b);
+  };
+  for (int l = 0; l < t.n_layers; ++l) {
+    add(kf.L.A1[l], kf.L.dA1[l], 0, 1.0 / (Bd * n), 0, 0.0);
+    add(kf.L.G1[l], t.d1, 0, 1.0 / Bd, 0, 0.0);
+  }
+  for (int l = 0; l < t.n_layers - 1; ++l) {
+    add(kf.L.A2[l], kf.L.dA2[l], 0, 1.0 / (Bd * n * n), 1, Bd * n * n);
+    add(kf.L.G2[l], t.d2, 0, 1.0 / Bd, 0, 0.0);
+  }
+  for (int sp = 0; sp < 2; ++sp) {
+    const double ns = sp == 0 ? t.n_up : t.n_down;
+    add(kf.L.Ao[sp], t.d1 + 1, 0, ns > 0 ? 1.0 / (Bd * ns) : 0.0, 0, 0.0);
+    add(kf.L.Go[sp], kf.L.dGo[sp], 0, 1.0 / Bd, 0, 0.0);
+  }
+  add(kf.L.D, kf.L.total - kf.L.D, 1, 1.0 / Bd, 0, 0.0);
+  KfacBlock* d_blk = reinterpret_cast<KfacBlock*>(c->ws);  // the workspace is free again
+  CK(cudaMemcpyAsync(d_blk, blk.data(), sizeof(KfacBlock) * blk.size(), cudaMemcpyHostToDevice, s));
+  launch_kfac_finalize(s, F, d_blk, (int)blk.size());
+  CK(cudaStreamSynchronize(s));  // the block table lives in pageable host memory
   return after_launch(c);
 }
 
@@ -1651,6 +1829,107 @@ fn_status ferminet_set_train_opts(fn_ctx* c, const fn_train_opts* o) {
     c->step_exec = nullptr;
   }
   return FN_OK;
+}
+
+fn_status ferminet_kfac_size(const fn_net* net, long* n_doubles) {
+  if (!net || !n_doubles) return FN_EINVAL;
+  long np = 0;
+  int ne = 0;
+  fn_status st = ferminet_net_layout(net, nullptr, 0, &ne, &np);
+  if (st != FN_OK) return st;
+  Layout lay;
+  build_layout(*net, &lay, false);
+  KfacLayout K;
+  kfac_layout(*net, lay, &K);
+  *n_doubles = K.total;
+  return FN_OK;
+}
+
+fn_status ferminet_kfac_factors(fn_ctx* c, const float* d_x, long B, double* d_factors) {
+  if (!c) return FN_EINVAL;
+  fn_status st = check_batch(c, d_x, B);
+  if (st != FN_OK) return st;
+  if (B < 1 || !d_factors) return fail(c, FN_EINVAL, "empty batch or null factor buffer");
+  if (!tc_store_ok(c)) return fail(c, FN_EINVAL, "KFAC factors need a mixed-precision context (tensor-core adjoint)");
+  return run_kfac(c, d_x, B, d_factors);
+}
+
+fn_status ferminet_kfac_precondition(fn_ctx* c, const double* d_factors, const float* d_grad, float lambda,
+                                     float* d_out) {
+  if (!c) return FN_EINVAL;
+  if (!d_factors || !d_grad || !d_out) return fail(c, FN_EINVAL, "null factor, gradient or output pointer");
+  if (!(lambda > 0.f)) return fail(c, FN_EINVAL, "lambda must be positive");
+  const fn_net& t = c->net;
+  const Layout& Lo = c->lay;
+  cudaStream_t s = c->stream;
+  KfacLayout K;
+  kfac_layout(t, Lo, &K);
+  // blocks to invert, each with its slot in the two inversion workspaces
+  struct Blk {
+    long W_off, b_off, rows, cols;  // gradient block [rows][cols - 1] + bias [rows]
+    int gi, ai;                     // indices of its G and A factors in the table
+  };
+  std::vector<KfacBlock> tab;
+  std::vector<Blk> work;
+  long wsz = 0, maxd = 0, maxm = 0;
+  auto fac = [&](long off, long dim) {
+    KfacBlock b{};
+    b.off = off;
+    b.dim = dim;
+    b.woff = wsz;
+    wsz += dim * dim;
+    maxd = std::max(maxd, dim);
+    tab.push_back(b);
+    return (int)tab.size() - 1;
+  };
+  for (int l = 0; l < t.n_layers; ++l) {
+    const long a = K.dA1[l];
+    work.push_back({Lo.V[l], Lo.b[l], (long)t.d1, a, fac(K.G1[l], t.d1), fac(K.A1[l], a)});
+  }
+  for (int l = 0; l < t.n_layers - 1; ++l) {
+    const long a = K.dA2[l];
+    work.push_back({Lo.W[l], Lo.c[l], (long)t.d2, a, fac(K.G2[l], t.d2), fac(K.A2[l], a)});
+  }
+  for (int sp = 0; sp < 2; ++sp) {
+    if (K.dGo[sp] == 0) continue;
+    const long wo = sp == 0 ? Lo.w_orb : Lo.w_orb + (long)t.n_det * t.n_up * t.d1;
+    const long go = sp == 0 ? Lo.g_orb : Lo.g_orb + (long)t.n_det * t.n_up;
+    work.push_back({wo, go, K.dGo[sp], (long)t.d1 + 1, fac(K.Go[sp], K.dGo[sp]), fac(K.Ao[sp], t.d1 + 1)});
+  }
+  for (const Blk& b : work) maxm = std::max(maxm, b.rows * b.cols);
+  // workspace: block table, two FP64 inversion copies, FP32 inverses and products
+  const size_t bytes = 256 * ((sizeof(KfacBlock) * tab.size() + 255) / 256) + sizeof(double) * 2 * wsz +
+                       sizeof(float) * (wsz + 3 * maxm) + 1024;
+  fn_status st = ensure_ws(c, bytes);
+  if (st != FN_OK) return st;
+  Arena ar;
+  ar.measure = false;
+  ar.base = c->ws;
+  KfacBlock* d_tab = ar.get<KfacBlock>(tab.size());
+  double* w0 = ar.get<double>(wsz);
+  double* w1 = ar.get<double>(wsz);
+  float* inv32 = ar.get<float>(wsz);
+  float* M = ar.get<float>(maxm);
+  float* X = ar.get<float>(maxm);
+  float* Dl = ar.get<float>(maxm);
+  CK(cudaMemcpyAsync(d_tab, tab.data(), sizeof(KfacBlock) * tab.size(), cudaMemcpyHostToDevice, s));
+  launch_kfac_invert(s, d_factors, d_tab, (int)tab.size(), (int)maxd, std::sqrt((double)lambda), w0, w1);
+  for (const KfacBlock& b : tab)  // the inverse of a block of dimension d ends in w0 (d even) or w1 (d odd)
+    launch_to_float(s, (b.dim % 2 == 0 ? w0 : w1) + b.woff, inv32 + b.woff, b.dim * b.dim);
+  // grad entries not covered by a block (none with this layout) pass through
+  CK(cudaMemcpyAsync(d_out, d_grad, sizeof(float) * Lo.total, cudaMemcpyDeviceToDevice, s));
+  for (const Blk& b : work) {
+    const float* Gi = inv32 + tab[b.gi].woff;
+    const float* Ai = inv32 + tab[b.ai].woff;
+    launch_gather_wb(s, d_grad, b.W_off, b.b_off, b.rows, b.cols, M);
+    gemm_nn(s, b.rows, b.cols, b.rows, Gi, b.rows, M, b.cols, X, b.cols, Epi{});
+    gemm_nn(s, b.rows, b.cols, b.cols, X, b.cols, Ai, b.cols, Dl, b.cols, Epi{});
+    launch_scatter_wb(s, Dl, b.W_off, b.b_off, b.rows, b.cols, d_out);
+  }
+  launch_diag_precond(s, d_grad + Lo.pi[0], d_factors + K.D, Lo.total - Lo.pi[0], (double)lambda,
+                      d_out + Lo.pi[0]);
+  CK(cudaStreamSynchronize(s));  // the block table lives in pageable host memory
+  return after_launch(c);
 }
 
 fn_status ferminet_step(fn_ctx* c, float* d_x, float* d_logpsi, long B, int n_steps, float width, uint64_t seed,

@@ -278,6 +278,49 @@ void launch_spread_mean1(cudaStream_t s, const float* m1bar, long Bc, int n, int
 void launch_spread_mean2(cudaStream_t s, const float* m2bar, long Bc, int n, int n_up, int din2, float* ebar);
 void launch_add(cudaStream_t s, float* dst, const float* src, long n);
 
+// ---------------------------------------------------------------------------
+// KFAC (k_kfac.cu)
+// Transposed KFAC input rows: column c of row r is taken from the segment
+// whose column range holds c (source row r / row_div, BF16 hi + lo), the last
+// column is 1; rows r >= rows, and with spin >= 0 rows whose electron
+// (r % n) is not of that spin, are zero.
+struct KfacRows {
+  struct Seg {
+    const __nv_bfloat16* hi;
+    const __nv_bfloat16* lo;
+    long ld;
+    int col0, ncols;
+    long row_div;
+  } seg[3];
+  int nseg;
+  long rows;
+  int cols;
+  int spin, n, n_up;
+};
+// One factor block of the buffer: off (offset in the factor buffer), dim,
+// woff (offset in the inversion workspaces), diag (a diagonal block of dim
+// entries), scale (sum -> average), and for the two-electron input factors
+// mirror_bias with the row count.
+struct KfacBlock {
+  long off, dim, woff;
+  int diag, mirror_bias;
+  double scale, count;
+};
+void launch_kfac_rows(cudaStream_t s, const KfacRows& a, __nv_bfloat16* hi, __nv_bfloat16* lo, long ld_out);
+void launch_colsq_accum(cudaStream_t s, const float* X, long rows, long cols, long ldx, double* out);
+void launch_kfac_finalize(cudaStream_t s, double* F, const KfacBlock* d_blk, int nblk);
+// Damped copies of every non-diagonal block (gamma on the diagonal) inverted
+// in FP64 by Gauss-Jordan, one launch per pivot step alternating between the
+// workspaces w0 and w1 (each holding every block at its woff); a block of
+// dimension d is done after step d - 1, so its inverse ends in w0 when d is
+// even and in w1 when d is odd.
+void launch_kfac_invert(cudaStream_t s, const double* F, const KfacBlock* d_blk, int nblk, int max_dim, double gamma,
+                        double* w0, double* w1);
+void launch_to_float(cudaStream_t s, const double* a, float* b, long n);
+void launch_gather_wb(cudaStream_t s, const float* g, long w_off, long b_off, long rows, long cols, float* M);
+void launch_scatter_wb(cudaStream_t s, const float* M, long w_off, long b_off, long rows, long cols, float* g);
+void launch_diag_precond(cudaStream_t s, const float* g, const double* D, long n, double lambda, float* out);
+
 }  // namespace fn
 
 // ---------------------------------------------------------------------------
