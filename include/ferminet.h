@@ -300,7 +300,11 @@ fn_status ferminet_step(fn_ctx* ctx, float* d_x, float* d_logpsi, long B, int n_
  *   adjoint_simt:  FN_PREC_MIXED only: 1 = the adjoint (its stored value
  *                  pass and its contractions) runs on the FP32 SIMT GEMMs;
  *                  0 = on the tensor cores with BF16 hi + lo operands and FP32
- *                  accumulation (default).  Not varied by the autotuner. */
+ *                  accumulation (default).  Not varied by the autotuner;
+ *   orbital_joint: FN_PREC_MIXED only: 1 = one orbital GEMM over every row and
+ *                  all K n orbitals; 0 = one per spin, each spin's electrons
+ *                  against that spin's orbitals only (half the work; default).
+ *                  Not varied by the autotuner. */
 typedef struct {
   int layer_groups;
   int feature_tile;
@@ -308,6 +312,7 @@ typedef struct {
   int residual_smem;
   int pair_unfused;
   int adjoint_simt;
+  int orbital_joint;
 } fn_tuning;
 
 fn_status ferminet_get_tuning(const fn_ctx* ctx, fn_tuning* out);

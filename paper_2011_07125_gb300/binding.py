@@ -37,7 +37,8 @@ class FnGeometry(C.Structure):
 
 class FnTuning(C.Structure):
     _fields_ = [("layer_groups", C.c_int), ("feature_tile", C.c_int), ("tangent_chunk", C.c_long),
-                ("residual_smem", C.c_int), ("pair_unfused", C.c_int), ("adjoint_simt", C.c_int)]
+                ("residual_smem", C.c_int), ("pair_unfused", C.c_int), ("adjoint_simt", C.c_int),
+                ("orbital_joint", C.c_int)]
 
 
 class FnTrainOpts(C.Structure):
@@ -326,7 +327,8 @@ class FermiNet:
     @staticmethod
     def _tdict(t):
         return {"layer_groups": t.layer_groups, "feature_tile": t.feature_tile, "tangent_chunk": t.tangent_chunk,
-                "residual_smem": t.residual_smem, "pair_unfused": t.pair_unfused, "adjoint_simt": t.adjoint_simt}
+                "residual_smem": t.residual_smem, "pair_unfused": t.pair_unfused, "adjoint_simt": t.adjoint_simt,
+                "orbital_joint": t.orbital_joint}
 
     def get_tuning(self):
         t = FnTuning()
@@ -334,9 +336,9 @@ class FermiNet:
         return self._tdict(t)
 
     def set_tuning(self, layer_groups=0, feature_tile=0, tangent_chunk=0, residual_smem=0, pair_unfused=0,
-                   adjoint_simt=0):
+                   adjoint_simt=0, orbital_joint=0):
         t = FnTuning(int(layer_groups), int(feature_tile), int(tangent_chunk), int(residual_smem), int(pair_unfused),
-                     int(adjoint_simt))
+                     int(adjoint_simt), int(orbital_joint))
         self._check(self.lib.ferminet_set_tuning(self.ctx, C.byref(t)), "ferminet_set_tuning")
 
     def autotune(self, x, repeats=2):

@@ -535,38 +535,79 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     {
       const double same_spin = (double)t.n_up * t.n_up + (double)t.n_down * t.n_down;
       Prof pg(c, tangent ? FN_KC_TANGENT_GEMM : FN_KC_COUNT, 2.0 * (double)Bc * Creal * d1 * K * same_spin);
-      TcGemmArgs o{};
-      const bool rm = Ktot % 4 == 0;
-      bool ok;
-      if (rm) {
-        int ntf = 1;
-        const int tf = feature_tile(Ktot, &ntf, c->tune.feature_tile);
-        ok = tc_segment_rm(o, 0, Hcb[0], Hcb[1], rows, ldh, c->wb_hi + c->wb_orb,
-                           two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb, tf);
-        o.rm = 1;
-        o.tile_n = tf;
-        o.n_tiles_n = ntf;
-        o.n_tiles_m = (int)((rows + 127) / 128);
-      } else {
-        const int to = plain_tile(rows);
-        ok = tc_segment(o, 0, c->wb_hi + c->wb_orb, two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb, Hcb[0],
-                        Hcb[1], rows, ldh, to);
-        o.tile_n = to;
-        o.n_tiles_n = (int)((rows + to - 1) / to);
-        o.n_tiles_m = (int)((Ktot + 127) / 128);
+      // Per spin when the shapes allow: electron j of spin s only meets the
+      // orbitals of spin s (Eq. 3), so each spin's rows (a block of n_s C rows
+      // per walker, through a 3-D tensor map) meet that spin's K n_s orbitals;
+      // the other-spin blocks of O are never computed nor read.
+      const long q_up = (long)K * t.n_up;
+      const bool per_spin = c->tune.orbital_joint == 0 && Ktot % 4 == 0 && q_up % 4 == 0 && t.n_up > 0 &&
+                            t.n_down > 0;
+      for (int sp = 0; sp < (per_spin ? 2 : 1); ++sp) {
+        TcGemmArgs o{};
+        const bool rm = Ktot % 4 == 0;
+        const long q0 = per_spin && sp == 1 ? q_up : 0;
+        const long nq = per_spin ? (long)K * (sp == 0 ? t.n_up : t.n_down) : Ktot;
+        bool ok;
+        if (per_spin) {
+          const long ns = sp == 0 ? t.n_up : t.n_down, s_off = sp == 0 ? 0 : t.n_up;
+          int ntf = 1;
+          const int tf = feature_tile(nq, &ntf, c->tune.feature_tile);
+          o.blk = 1;
+          o.blk_rows = ns * C;
+          o.blk_stride = (long)n * C;
+          o.blk_off = s_off * C;
+          o.n_blk = Bc;
+          o.box_y = (int)std::min<long>(o.blk_rows, 128);
+          o.box_z = o.blk_rows >= 128 ? 1 : (int)(128 / o.blk_rows);
+          o.tiles_per_blk = (int)((o.blk_rows + o.box_y - 1) / o.box_y);
+          const __nv_bfloat16* a_hi = Hcb[0] + o.blk_off * ldh;
+          const __nv_bfloat16* a_lo = two ? Hcb[1] + o.blk_off * ldh : nullptr;
+          const __nv_bfloat16* w_hi = c->wb_hi + c->wb_orb + q0 * c->ld_orb;
+          const __nv_bfloat16* w_lo = two ? c->wb_lo + c->wb_orb + q0 * c->ld_orb : nullptr;
+          ok = ldh == c->ld_orb && tc_make_map3(&o.A[0][0], a_hi, o.blk_rows, Bc, o.blk_stride, ldh, o.box_y, o.box_z) &&
+               tc_make_map(&o.B[0][0], w_hi, nq, ldh, tf);
+          if (two)
+            ok = ok && tc_make_map3(&o.A[0][1], a_lo, o.blk_rows, Bc, o.blk_stride, ldh, o.box_y, o.box_z) &&
+                 tc_make_map(&o.B[0][1], w_lo, nq, ldh, tf);
+          else {
+            o.A[0][1] = o.A[0][0];
+            o.B[0][1] = o.B[0][0];
+          }
+          o.kblocks[0] = (int)(ldh / 64);
+          o.rm = 1;
+          o.tile_n = tf;
+          o.n_tiles_n = ntf;
+          o.n_tiles_m = (int)(o.box_z == 1 ? Bc * o.tiles_per_blk : (Bc + o.box_z - 1) / o.box_z);
+        } else if (rm) {
+          int ntf = 1;
+          const int tf = feature_tile(Ktot, &ntf, c->tune.feature_tile);
+          ok = tc_segment_rm(o, 0, Hcb[0], Hcb[1], rows, ldh, c->wb_hi + c->wb_orb,
+                             two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb, tf);
+          o.rm = 1;
+          o.tile_n = tf;
+          o.n_tiles_n = ntf;
+          o.n_tiles_m = (int)((rows + 127) / 128);
+        } else {
+          const int to = plain_tile(rows);
+          ok = tc_segment(o, 0, c->wb_hi + c->wb_orb, two ? c->wb_lo + c->wb_orb : nullptr, Ktot, c->ld_orb,
+                          Hcb[0], Hcb[1], rows, ldh, to);
+          o.tile_n = to;
+          o.n_tiles_n = (int)((rows + to - 1) / to);
+          o.n_tiles_m = (int)((Ktot + 127) / 128);
+        }
+        o.nseg = 1;
+        o.terms = c->terms;
+        o.seg_terms[0] = c->terms;
+        o.rows = rows;
+        o.mfeat = (int)nq;
+        o.mode = 0;
+        o.out = O + q0;
+        o.ldo = Ktot;
+        o.bias = P + c->lay.g_orb + q0;
+        o.bias_period = C;
+        o.status = c->d_status;
+        if (!ok || tc_gemm_launch(s, o) != FN_OK) c->host_fail = true;
       }
-      o.nseg = 1;
-      o.terms = c->terms;
-      o.seg_terms[0] = c->terms;
-      o.rows = rows;
-      o.mfeat = (int)Ktot;
-      o.mode = 0;
-      o.out = O;
-      o.ldo = Ktot;
-      o.bias = P + c->lay.g_orb;
-      o.bias_period = C;
-      o.status = c->d_status;
-      if (!ok || tc_gemm_launch(s, o) != FN_OK) c->host_fail = true;
     }
   }
   for (int l = 0; l < L && !tc; ++l) {
@@ -2022,7 +2063,7 @@ fn_status ferminet_set_tuning(fn_ctx* c, const fn_tuning* t) {
   if (!c || !t) return FN_EINVAL;
   if (t->layer_groups < 0 || t->feature_tile < 0 || t->tangent_chunk < 0 || t->residual_smem < 0 ||
       t->residual_smem > 1 || t->pair_unfused < 0 || t->pair_unfused > 1 || t->adjoint_simt < 0 ||
-      t->adjoint_simt > 1)
+      t->adjoint_simt > 1 || t->orbital_joint < 0 || t->orbital_joint > 1)
     return fail(c, FN_EINVAL, "bad tuning value");
   if (t->layer_groups > 0 && (t->layer_groups * c->Ct > 256 || (t->layer_groups * c->Ct) % 16))
     return fail(c, FN_EINVAL, "layer_groups gives an invalid tile");

@@ -104,6 +104,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Row-block tile origin (see TcGemmArgs::blk).
+__device__ __forceinline__ void blk_origin(const TcGemmArgs& a, int tm, int& y0, int& z0) {
+  if (a.box_z == 1) {
+    z0 = tm / a.tiles_per_blk;
+    y0 = (tm % a.tiles_per_blk) * a.box_y;
+  } else {
+    z0 = tm * a.box_z;
+    y0 = 0;
+  }
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
 // 1024 bytes (stride-dimension byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -303,6 +322,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
           if (it.res) {
             mbar_expect_tx(&full[stage], A_BYTES);
             tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
+          } else if (a.blk) {
+            // row blocks: the box's rows (box_y * box_z of them) land packed at the
+            // start of the A tile; the rest of the tile is not read back
+            int y0, z0;
+            blk_origin(a, tm, y0, z0);
+            mbar_expect_tx(&full[stage], (uint32_t)(a.box_y * a.box_z * BK * 2) + b_bytes);
+            tma_load_3d(sa, &a.A[sg][ai], kb * BK, y0, z0, &full[stage]);
+            tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
           } else if (a.seg_group[sg] == 0) {
             mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
             tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
@@ -418,8 +445,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       if (a.rm) {
         // rows on TMEM lanes: this thread owns row r and reads 8 features per
         // tcgen05.ld; loads and stores are 16-byte vectors along the features
-        const long r = (long)tm * BM + lane_base + lane;
-        const bool rok = r < a.rows;
+        long r = (long)tm * BM + lane_base + lane;
+        bool rok = r < a.rows;
+        if (a.blk) {  // lane row t of a row-block tile
+          int y0, z0;
+          blk_origin(a, tm, y0, z0);
+          const int tr = lane_base + lane;
+          const long zb = z0 + tr / a.box_y, yb = y0 + tr % a.box_y;
+          rok = tr < a.box_y * a.box_z && zb < a.n_blk && yb < a.blk_rows;
+          r = zb * a.blk_stride + a.blk_off + yb;
+        }
         const int ldb = (int)a.ldhb;
         const float* __restrict__ urow = (a.mode == 2 && rok) ? Up + (r / a.u_div) * a.ldu : nullptr;
         for (int f0 = half * 8; f0 < tile_n; f0 += 16) {
@@ -721,6 +756,22 @@ bool tc_make_map(CUtensorMap* tm, const void* base, long rows, long ld_elems, in
   return r == CUDA_SUCCESS;
 }
 
+bool tc_make_map3(CUtensorMap* tm, const void* base, long blk_rows, long n_blk, long blk_stride, long ld_elems,
+                  int box_y, int box_z) {
+  if (!tc_encode_ready()) return false;
+  if (((uintptr_t)base & 15) || (ld_elems % BK) || blk_rows < 1 || n_blk < 1 || box_y < 1 || box_y > 256 ||
+      box_z < 1 || box_z > 256)
+    return false;
+  cuuint64_t dims[3] = {(cuuint64_t)ld_elems, (cuuint64_t)blk_rows, (cuuint64_t)n_blk};
+  cuuint64_t strides[2] = {(cuuint64_t)ld_elems * 2, (cuuint64_t)blk_stride * ld_elems * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_y, (cuuint32_t)box_z};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
   static PerDeviceOnce attr;  // the attribute is per function and device
   attr([] { cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES); });
@@ -746,6 +797,10 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
                        (long)(a.ksplit - 1) * a.kb_per_split >= a.kblocks[0] || a.split_stride < 1))
     return FN_EINVAL;
   if (a.y_out && (!a.rm || a.mode != 2 || a.ldy % 4 || ((uintptr_t)a.y_out & 15))) return FN_EINVAL;
+  if (a.blk && (!a.rm || a.nseg != 1 || a.ksplit > 1 || a.box_y < 1 || a.box_z < 1 || a.box_y * a.box_z > BM ||
+                a.box_y > 256 || a.box_z > 256 || a.blk_rows < 1 || a.n_blk < 1 ||
+                (a.box_z == 1 ? a.tiles_per_blk < 1 : a.box_y < a.blk_rows)))
+    return FN_EINVAL;
   for (int sg = 0; sg < a.nseg; ++sg) {
     if (a.seg_terms[sg] < 1 || a.seg_terms[sg] > 3 || a.kblocks[sg] < 1) return FN_EINVAL;
     if (a.seg_group[sg] && (a.seg_group[sg] % 8 || a.tile_n % a.seg_group[sg] || a.u_div < 1)) return FN_EINVAL;

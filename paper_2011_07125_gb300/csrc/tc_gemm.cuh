@@ -56,11 +56,25 @@ struct TcGemmArgs {
   // also stored as FP32 [rows][ldy]
   float* y_out;
   long ldy;
+  // rows on lanes, row blocks: the A rows are blocks of blk_rows rows that
+  // start every blk_stride rows (at blk_off within the stride; n_blk blocks),
+  // loaded through a 3-D tensor map {ld, blk_rows, n_blk} in boxes of box_y rows
+  // of box_z blocks (box_y * box_z <= 128).  Tile tm covers rows
+  // [y0, y0 + box_y) of blocks [z0, z0 + box_z): with box_z == 1,
+  // z0 = tm / tiles_per_blk and y0 = (tm % tiles_per_blk) * box_y; else z0 =
+  // tm * box_z and y0 = 0.  Output rows are z * blk_stride + blk_off + y.
+  int blk;
+  long blk_rows, blk_stride, blk_off, n_blk;
+  int box_y, box_z, tiles_per_blk;
   unsigned* status;
 };
 
 bool tc_encode_ready();
 bool tc_make_map(CUtensorMap* tm, const void* base, long rows, long ld_elems, int box_rows);
+// 3-D map {ld_elems, blk_rows, n_blk} with block stride blk_stride rows, box
+// {64, box_y, box_z}.
+bool tc_make_map3(CUtensorMap* tm, const void* base, long blk_rows, long n_blk, long blk_stride, long ld_elems,
+                  int box_y, int box_z);
 fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a);
 
 }  // namespace fn

@@ -65,7 +65,7 @@ def test_kfac_step_matches_oracle_and_needs_mixed():
     """Factors and update of the VMC gradient, end to end on the device,
     against the oracle's pipeline; an FP32 context refuses the factors."""
     from paper_2011_07125_gb300.binding import FermiNetError
-    wl, lay, P, x, geo = setup("c4h4x8", 1)
+    wl, lay, P, x, geo = setup("c4h4x8", 2)  # two walkers per geometry: a non-zero gradient
     fn = _make(wl, P)
     xx = torch.from_numpy(x).cuda()
     eloc = (np.random.default_rng(4).standard_normal(len(x)) * 2 - 7).astype(np.float32)

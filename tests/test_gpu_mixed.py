@@ -139,3 +139,23 @@ def test_mixed_logpsi_vjp_blocks(name, per):
         if nb > 1e-6 * np.linalg.norm(g_o):
             assert np.linalg.norm(g_tc[sl] - g_o[sl]) / nb < TOL_GRAD_MIXED, e.name
     assert err < TOL_GRAD_MIXED
+
+
+@pytest.mark.parametrize("name,per", [("ne", 12), ("c4h6", 3), ("c4h4x8", 2), ("li", 8)])
+def test_orbitals_per_spin_equal_joint(name, per):
+    """The per-spin orbital GEMMs (row blocks through a 3-D tensor map, each
+    spin's electrons against its own orbitals) give the joint GEMM's results:
+    same operands and accumulation order for every same-spin entry."""
+    wl, lay, P, x, geo = setup(name, per)
+    fn = make(wl, P, "mixed")
+    xx = torch.from_numpy(x).cuda()
+    res = []
+    for joint in (0, 1):
+        fn.set_tuning(orbital_joint=joint)
+        lp = fn.logpsi(xx)[0]
+        out = fn.local_energy(xx)
+        g = fn.logpsi_vjp(xx, torch.linspace(-1, 1, len(x), device="cuda"))
+        assert fn.sync() == "FN_OK"
+        res.append((lp, out["eloc"], out["logpsi"], g))
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
