@@ -200,6 +200,53 @@ __device__ __forceinline__ int tile_items(const TcGemmArgs& a, int tm, int z) {
   return n;
 }
 
+// The same sequence as item_at, walked incrementally (no divisions): the
+// producer and the MMA issuer are single threads whose per-item instruction
+// count bounds the pipeline.
+struct ItemWalk {
+  Item it;
+  int end, nres, tm;
+};
+
+__device__ __forceinline__ void walk_fix(const TcGemmArgs& a, ItemWalk& w) {
+  while (!w.it.res && w.it.kb >= w.end) {
+    if (++w.it.sg < a.nseg) {
+      w.it.kb = 0;
+      w.end = a.kblocks[w.it.sg];
+    } else {
+      w.it.res = true;
+      w.it.sg = 0;
+      w.it.kb = 2 * w.tm;
+      w.end = 2 * w.tm + w.nres;
+    }
+  }
+}
+
+__device__ __forceinline__ void walk_begin(const TcGemmArgs& a, int tm, int nres, int z, ItemWalk& w) {
+  w.tm = tm;
+  w.nres = nres;
+  w.it.res = false;
+  w.it.sg = 0;
+  w.it.t = 0;
+  if (a.ksplit > 1) {
+    w.it.kb = split_kb0(a, z);
+    w.end = w.it.kb + split_nkb(a, z);
+    return;
+  }
+  w.it.kb = (nres > 0 && tm == 0) ? nres : 0;  // residual k-blocks come last
+  w.end = a.kblocks[0];
+  walk_fix(a, w);
+}
+
+__device__ __forceinline__ void walk_next(const TcGemmArgs& a, ItemWalk& w) {
+  if (++w.it.t < a.seg_terms[w.it.sg]) return;
+  w.it.t = 0;
+  ++w.it.kb;
+  if (w.it.res || a.ksplit > 1) return;
+  if (w.it.sg == 0 && w.nres > 0 && w.it.kb == 2 * w.tm) w.it.kb += w.nres;
+  walk_fix(a, w);
+}
+
 __device__ __forceinline__ Item item_at(const TcGemmArgs& a, int tm, int nres, int i, int z) {
   Item it;
   it.res = false;
@@ -295,9 +342,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         const int tn = (int)(tmn / a.n_tiles_m), tm = (int)(tmn % a.n_tiles_m);
         const int nres = res_blocks(a, tm);
         const int nit = tile_items(a, tm, z);
+        // rows of the per-walker tensor gathered for this tile's groups
+        int gy[32];
+        for (int sg = 0; sg < a.nseg; ++sg)
+          if (a.seg_group[sg]) {
+            const int G = a.seg_group[sg];
+            for (int gi = 0, g0 = 0; g0 < tile_n && gi < 32; g0 += G, ++gi) {
+              long r0 = (long)tn * tile_n + g0;
+              if (r0 >= a.rows) r0 = a.rows - G;  // past the end: any in-range rows (unused)
+              gy[gi] = (int)((r0 / a.u_div) * G);
+            }
+          }
+        ItemWalk wk;
+        walk_begin(a, tm, nres, z, wk);
         bool ok = true;
-        for (int i = 0; i < nit && ok; ++i) {
-          const Item it = item_at(a, tm, nres, i, z);
+        for (int i = 0; i < nit && ok; ++i, walk_next(a, wk)) {
+          const Item it = wk.it;
           if (it.res && it.kb == 2 * tm && it.t == 0) {
             // the residual region is free once the previous tile's epilogue is done
             if (!mbar_wait(rempty, rphase ^ 1, abort_flag, a.status)) {
@@ -340,12 +400,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             mbar_expect_tx(&full[stage], A_BYTES + b_bytes);
             const int G = a.seg_group[sg];
             tma_load_2d(sa, &a.A[sg][ai], kb * BK, 0, &full[stage]);
-            for (int g0 = 0; g0 < tile_n; g0 += G) {
-              long r0 = (long)tn * tile_n + g0;
-              if (r0 >= a.rows) r0 = a.rows - G;  // past the end: any in-range rows (unused)
-              const int y = (int)((r0 / a.u_div) * G);
-              tma_load_2d(sb + (size_t)g0 * BK * 2, &a.B[sg][bi], tm * BM + kb * BK, y, &full[stage]);
-            }
+            for (int gi = 0, g0 = 0; g0 < tile_n; g0 += G, ++gi)
+              tma_load_2d(sb + (size_t)g0 * BK * 2, &a.B[sg][bi], tm * BM + kb * BK, gy[gi], &full[stage]);
           }
           if (++stage == nst) {
             stage = 0;
@@ -373,8 +429,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
         bool ok = true;
         uint32_t first = 1;
-        for (int i = 0; i < nit && ok; ++i) {
-          const Item it = item_at(a, tm, nres, i, z);
+        ItemWalk wk;
+        walk_begin(a, tm, nres, z, wk);
+        for (int i = 0; i < nit && ok; ++i, walk_next(a, wk)) {
+          const Item it = wk.it;
           if (it.res && it.kb == 2 * tm && it.t == 0) {
             if (!mbar_wait(rfull, rphase, abort_flag, a.status)) {
               ok = false;
@@ -803,7 +861,9 @@ fn_status tc_gemm_launch(cudaStream_t s, const TcGemmArgs& a0) {
     return FN_EINVAL;
   for (int sg = 0; sg < a.nseg; ++sg) {
     if (a.seg_terms[sg] < 1 || a.seg_terms[sg] > 3 || a.kblocks[sg] < 1) return FN_EINVAL;
-    if (a.seg_group[sg] && (a.seg_group[sg] % 8 || a.tile_n % a.seg_group[sg] || a.u_div < 1)) return FN_EINVAL;
+    if (a.seg_group[sg] && (a.seg_group[sg] % 8 || a.tile_n % a.seg_group[sg] || a.u_div < 1 ||
+                            a.tile_n / a.seg_group[sg] > 32))
+      return FN_EINVAL;
   }
   const long total = (long)a.n_tiles_n * a.n_tiles_m * (a.ksplit > 1 ? a.ksplit : 1);
   if (total <= 0) return FN_OK;
