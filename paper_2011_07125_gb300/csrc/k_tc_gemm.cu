@@ -247,6 +247,16 @@ __device__ __forceinline__ void walk_next(const TcGemmArgs& a, ItemWalk& w) {
   walk_fix(a, w);
 }
 
+// Operand reuse across the split terms of one k-block.  With nt terms the
+// k-block's items are t = 0 (A_hi B_hi), 1 (A_hi B_lo), 2 (A_lo B_hi).  A ring
+// slot holds an A part and a B part; the k-block fills at most two slots:
+//   plain k-block: t = 0 loads {A_hi, B_hi}, t = 1 loads {A_lo (if nt == 3), B_lo},
+//                  t = 2 loads nothing (A_lo from the second slot, B_hi from the first);
+//   residual k-block (B from the residual region): t = 0 loads {A_hi}, t = 1
+//                  loads nothing, t = 2 loads {A_lo}.
+// Both slots are released after the k-block's last MMA.
+__device__ __forceinline__ bool item_loads(const Item& it) { return it.res ? it.t != 1 : it.t != 2; }
+
 __device__ __forceinline__ Item item_at(const TcGemmArgs& a, int tm, int nres, int i, int z) {
   Item it;
   it.res = false;
@@ -371,17 +381,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                 tma_load_2d(resr + h * res_half + r * (a.tile_n * BK * 2), &a.B[0][h], (2 * tm + r) * BK,
                             tn * tile_n, rfull);
           }
+          if (!item_loads(it)) continue;  // operands already in the k-block's slots
           if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status)) {
             ok = false;
             break;
           }
-          const int ai = (it.t == 2) ? 1 : 0, bi = (it.t == 1) ? 1 : 0;
+          // part (hi 0 / lo 1) of each operand this load brings
+          const int ai = it.t == 0 ? 0 : 1, bi = it.t == 0 ? 0 : 1;
+          const bool need_a = it.res || it.t == 0 || a.seg_terms[it.sg] == 3;
           uint8_t* sa = smem + stage * stage_bytes;
           uint8_t* sb = sa + A_BYTES;
           const int sg = it.sg, kb = it.kb;
           if (it.res) {
             mbar_expect_tx(&full[stage], A_BYTES);
             tma_load_2d(sa, &a.A[sg][ai], kb * BK, tm * BM, &full[stage]);
+          } else if (!need_a) {
+            // second slot of a two-term k-block: B_lo only (the identity segment)
+            mbar_expect_tx(&full[stage], b_bytes);
+            if (a.seg_group[sg] == 0) {
+              tma_load_2d(sb, &a.B[sg][bi], kb * BK, tn * tile_n, &full[stage]);
+            } else {
+              const int G = a.seg_group[sg];
+              for (int gi = 0, g0 = 0; g0 < tile_n; g0 += G, ++gi)
+                tma_load_2d(sb + (size_t)g0 * BK * 2, &a.B[sg][bi], tm * BM + kb * BK, gy[gi], &full[stage]);
+            }
           } else if (a.blk) {
             // row blocks: the box's rows (box_y * box_z of them) land packed at the
             // start of the A tile; the rest of the tile is not read back
@@ -419,6 +442,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       uint32_t phase = 0, rphase = 0;
       int acc = 0;
       uint32_t acc_phase = 0;
+      int s0 = 0, s1 = 0;  // slots of the current k-block (first and second load)
       for (long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int z = (int)(tile / mn_tiles);
         const int tm = (int)((tile % mn_tiles) % a.n_tiles_m);
@@ -439,16 +463,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
               break;
             }
           }
-          if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
-            ok = false;
-            break;
+          const int nt = a.seg_terms[it.sg];
+          if (item_loads(it)) {
+            if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            if (it.t == 0) s0 = stage;
+            else s1 = stage;
+            if (++stage == nst) {
+              stage = 0;
+              phase ^= 1;
+            }
           }
-          fence_after();
-          const uint32_t sa = smem_u32(smem + stage * stage_bytes);
-          uint32_t sb = sa + A_BYTES;
+          const uint32_t a0 = smem_u32(smem + s0 * stage_bytes), a1 = smem_u32(smem + s1 * stage_bytes);
+          uint32_t sa, sb;
           if (it.res) {
-            const int bi = (it.t == 1) ? 1 : 0;
-            sb = smem_u32(resr + bi * res_half + (it.kb - 2 * tm) * (a.tile_n * BK * 2));
+            // B from the residual region: hi for t = 0, 2; lo for t = 1
+            sb = smem_u32(resr + (it.t == 1 ? res_half : 0) + (it.kb - 2 * tm) * (a.tile_n * BK * 2));
+            sa = it.t == 2 ? a1 : a0;
+          } else {
+            sa = it.t == 2 ? a1 : a0;                           // A_hi (slot 0) or A_lo (slot 1)
+            sb = (it.t == 1 ? a1 : a0) + A_BYTES;               // B_hi (slot 0) or B_lo (slot 1)
           }
           const uint64_t da = smem_desc(sa), db = smem_desc(sb);
 #pragma unroll
@@ -457,10 +494,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, first ? 0u : 1u);
             first = 0;
           }
-          mma_commit(&empty[stage]);
-          if (++stage == nst) {
-            stage = 0;
-            phase ^= 1;
+          if (it.t == nt - 1) {  // the k-block's last term: release its slots
+            mma_commit(&empty[s0]);
+            if (nt > 1) mma_commit(&empty[s1]);
           }
         }
         if (!ok) break;
