@@ -47,7 +47,8 @@ constexpr int BAR_BYTES = 256;
 // address and the abort flag
 static_assert((2 * MAX_STAGES + 4 + 2) * 8 + 8 <= BAR_BYTES, "barrier region too small");
 constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
+constexpr int NSL = EPI_WARPS / 4;  // epilogue warps per TMEM lane quarter (slices)
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -290,7 +291,9 @@ __device__ __forceinline__ Item item_at(const TcGemmArgs& a, int tm, int nres, i
 
 __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ TcGemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, derived from smem_raw by pointer arithmetic so that
+  // the compiler keeps the shared address space (shared loads, not generic ones)
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int nst = a.stages;
   const int stage_bytes = A_BYTES + a.tile_n * BK * 2;
   uint8_t* resr = smem + nst * stage_bytes;                   // residual region (1024-aligned)
@@ -509,10 +512,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       }
     }
   } else {
-    // epilogue warps 2..9: TMEM lane quarter = warp % 4; the two warps of a
-    // quarter split the tile's column chunks (plain) or groups (layer)
+    // epilogue warps: TMEM lane quarter = warp % 4; the NSL warps (slices) of a
+    // quarter split the tile's column chunks (plain) or groups and their
+    // column chunks (layer)
     const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int sl = (warp - 2) >> 2;
     const int lane_base = quarter * 32;
     const float* __restrict__ Up = a.U;
     const float* __restrict__ bias = a.bias;
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         }
         const int ldb = (int)a.ldhb;
         const float* __restrict__ urow = (a.mode == 2 && rok) ? Up + (r / a.u_div) * a.ldu : nullptr;
-        for (int f0 = half * 8; f0 < tile_n; f0 += 16) {
+        for (int f0 = sl * 8; f0 < tile_n; f0 += 8 * NSL) {
           const int fb = tn * tile_n + f0;
           if (fb >= a.mfeat) break;  // warp-uniform
           float v[8];
@@ -662,22 +666,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
           }
         };
         float ua[8], ra[8], ub[8], rbv[8];
-        int c0 = half * 8;
+        int c0 = sl * 8;
         if (r_tile + c0 < a.rows) load8(ua, ra, r_tile + c0);
-        for (; c0 < tile_n; c0 += 32) {
+        for (; c0 < tile_n; c0 += 16 * NSL) {
           if (r_tile + c0 >= a.rows) break;  // warp-uniform
-          const int c1 = c0 + 16;
+          const int c1 = c0 + 8 * NSL;
           const bool more = c1 < tile_n && r_tile + c1 < a.rows;
           if (more) load8(ub, rbv, r_tile + c1);
           emit8(ua, ra, c0);
           if (!more) break;
-          const int c2 = c1 + 16;
+          const int c2 = c1 + 8 * NSL;
           if (c2 < tile_n && r_tile + c2 < a.rows) load8(ua, ra, r_tile + c2);
           emit8(ub, rbv, c1);
         }
       } else if (a.mode == 0) {
         const float bf = (fok && bias) ? bias[f] : 0.f;
-        for (int c0 = half * 8; c0 < tile_n; c0 += 16) {
+        for (int c0 = sl * 8; c0 < tile_n; c0 += 8 * NSL) {
           if (r_tile + c0 >= a.rows) break;  // warp-uniform
           float v[8];
           tmem_ld8(tbase + c0, v);
@@ -703,6 +707,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         // first and last chunks mix kinds.
         const int C = a.C, n3 = a.n3;
         const int groups = tile_n / C;
+        // P column parts per group (a power of two), gsl groups in flight
+        int P = 1;
+        while (2 * P <= NSL && 2 * P * groups <= NSL) P *= 2;
+        const int gsl = NSL / P, gs = sl % gsl, cp = sl / gsl;
         const float bf = (fok && bias) ? bias[f] : 0.f;
         const long ldb = a.ldhb;
         // residual in the shared region: 128-byte rows of 64 features whose
@@ -718,38 +726,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         for (int j = 0; j < 8; ++j) swz[j] = (uint32_t)(j * 128 + ((chunk ^ j) << 4));
         const bool slo = a.res_lo != nullptr;
         const bool gres = rh && !a.res_smem;
-        for (int gi = half; gi < groups; gi += 2) {
+        for (int gi = gs; gi < groups; gi += gsl) {
           const long r0 = r_tile + (long)gi * C;
           if (r0 >= a.rows) continue;  // warp-uniform: no TMEM access for groups past the end
           const uint32_t tg = tbase + (uint32_t)(gi * C);
-          // pass 1: value column and sum of squared derivative columns
-          float z0 = 0.f, sq = 0.f;
+          // pass 1 (every part of the group): value column and sum of squared
+          // derivative columns, in two partial sums
+          float z0 = 0.f, sq0 = 0.f, sq1 = 0.f;
           for (int c0 = 0; c0 < C; c0 += 8) {
             float v[8];
             tmem_ld8(tg + c0, v);
             if (c0 >= 1 && c0 + 7 <= n3) {
 #pragma unroll
-              for (int j = 0; j < 8; ++j) sq = fmaf(v[j], v[j], sq);
+              for (int j = 0; j < 8; j += 2) {
+                sq0 = fmaf(v[j], v[j], sq0);
+                sq1 = fmaf(v[j + 1], v[j + 1], sq1);
+              }
             } else {
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 const int c = c0 + j;
                 if (c == 0) z0 = v[j] + bf;
-                else if (c <= n3) sq = fmaf(v[j], v[j], sq);
+                else if (c <= n3) sq0 = fmaf(v[j], v[j], sq0);
               }
             }
           }
+          const float sq = sq0 + sq1;
           const float y = tanhf(z0);
           const float s = 1.f - y * y;
           const float lapc = -2.f * y * s * sq;
-          // pass 2: outputs (+ residual) as BF16 hi + lo, pointers advanced per chunk
-          const long rb = r0 * ldb + (fok ? f : 0);
-          __nv_bfloat16* ph = oh + rb;
-          __nv_bfloat16* pl = ol ? ol + rb : nullptr;
-          const __nv_bfloat16* gh = gres ? rh + rb : nullptr;
-          const __nv_bfloat16* gl = (gres && rl) ? rl + rb : nullptr;
-          const uint8_t* rs = rsh + (size_t)(gi * C) * 128;
-          for (int c0 = 0; c0 < C; c0 += 8) {
+          // pass 2 (this part's chunks): outputs (+ residual) as BF16 hi + lo
+          for (int c0 = cp * 8; c0 < C; c0 += 8 * P) {
+            const long rb = (r0 + c0) * ldb + (fok ? f : 0);
+            __nv_bfloat16* ph = oh + rb;
+            __nv_bfloat16* pl = ol ? ol + rb : nullptr;
+            const __nv_bfloat16* gh = gres ? rh + rb : nullptr;
+            const __nv_bfloat16* gl = (gres && rl) ? rl + rb : nullptr;
+            const uint8_t* rs = rsh + (size_t)(gi * C + c0) * 128;
             float v[8];
             tmem_ld8(tg + c0, v);
             if (fok) {
@@ -789,11 +802,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                 if (pl) pl[j * ldb] = __float2bfloat16_rn(o8[j] - __bfloat162float(h));
               }
             }
-            ph += 8 * ldb;
-            if (pl) pl += 8 * ldb;
-            if (gh) gh += 8 * ldb;
-            if (gl) gl += 8 * ldb;
-            rs += 8 * 128;
           }
         }
       }
