@@ -205,10 +205,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, prec: str):
+TRAFFIC_TUNING = ("layer_groups", "residual_smem")  # tuning fields a traffic record is keyed by
+
+
+def recorded_traffic(workload: str, prec: str, tuning=None):
     """DRAM bytes per walker of the timed GEMM class from the committed ncu
     summary (profiles/roofline_traffic.md), or None if the kernel sources have
-    changed since the capture."""
+    changed since the capture or the record's tuning (layer_groups,
+    residual_smem) differs from the timed one."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     if not os.path.exists(path):
         return None
@@ -217,8 +221,14 @@ def recorded_traffic(workload: str, prec: str):
         if not line.startswith("traffic:"):
             continue
         kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
-        if kv.get("workload") == workload and kv.get("precision") == prec and kv.get("source") == src:
-            return float(kv["bytes_per_walker"])
+        if kv.get("workload") != workload or kv.get("precision") != prec or kv.get("source") != src:
+            continue
+        if "tuning" in kv:
+            rec = dict(t.split(":", 1) for t in kv["tuning"].split(",") if ":" in t)
+            cur = tuning or {}
+            if any(int(rec.get(k, 0)) != int(cur.get(k, 0)) for k in TRAFFIC_TUNING):
+                continue
+        return float(kv["bytes_per_walker"])
     return None
 
 
@@ -241,7 +251,7 @@ def gemm_class_alg_bytes(net) -> float:
     return tot
 
 
-def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_launch=None, net=None):
+def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_launch=None, net=None, tuning=None):
     r = fn.profile_read("tangent_gemm")
     if r["launches"] == 0 or r["ms"] <= 0:
         return None
@@ -256,7 +266,7 @@ def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_l
     else:
         peak = _num(pk, "bf16_tflops_sustained", "bf16_tflops") or 1700.0
         bound, note = "tensor", f"bf16 sustained, {pk_kind}"
-    bpw = recorded_traffic(workload, prec) if workload else None
+    bpw = recorded_traffic(workload, prec, tuning) if workload else None
     traffic = bpw * walkers_per_launch if (bpw is not None and walkers_per_launch) else None
     hbm = None
     if net is not None and walkers_per_launch:
@@ -437,6 +447,42 @@ def envelope_overhead(flush, args):
     return res
 
 
+def run_eloc_pass(args, wl):
+    """One local-energy pass of the workload with every geometry's walker count
+    divided by --eloc-pass (at least one walker each), after --warmup passes:
+    the small case on which ncu captures the DRAM traffic of the tensor-core
+    GEMM class (only k_tc_gemm launches of local-energy passes run after the
+    context is set up).  Prints the walkers and tuning as one JSON line."""
+    import dataclasses
+    import torch
+    from paper_2011_07125_gb300 import synth
+    from paper_2011_07125_gb300.binding import FermiNet
+    div = args.eloc_pass
+    wl = dataclasses.replace(wl, counts=[max(1, c // div) for c in wl.counts])
+    prec = args.precision or wl.precision
+    fn = FermiNet(wl.net, wl.geoms, counts=wl.counts, precision=prec)
+    fn.set_params(torch.from_numpy(synth.init_params(fn.layout)).cuda())
+    x = torch.from_numpy(synth.init_walkers(wl)).cuda()
+    tuning = dict(t.split("=", 1) for t in args.pass_tuning.split(",") if "=" in t)
+    tuning = {k: int(v) for k, v in tuning.items()}
+    if prec == "mixed":
+        fn.set_tuning(**tuning)
+    for _ in range(args.warmup):
+        fn.local_energy(x)
+    torch.cuda.synchronize()
+    fn.profile(True)
+    fn.local_energy(x)
+    torch.cuda.synchronize()
+    r = fn.profile_read("tangent_gemm")
+    st = fn.sync()
+    print(json.dumps({"eloc_pass": wl.name, "walkers": wl.batch, "counts": wl.counts, "precision": prec,
+                      "tuning": tuning, "gemm_class_launches": r["launches"], "gemm_class_ms": r["ms"],
+                      "status": st}), flush=True)
+    fn.close()
+    if st != "FN_OK":
+        sys.exit(1)
+
+
 def run_gpu(args, wl):
     import numpy as np
     import torch
@@ -510,7 +556,7 @@ def run_gpu(args, wl):
     r_tg = fn.profile_read("tangent_gemm")
     passes = args.steps  # one local-energy pass per step
     roof = tangent_roofline(fn, prec, clocks, pk, pk_kind, wl.name,
-                            wl.batch * passes / max(r_tg["launches"], 1), net=wl.net)
+                            wl.batch * passes / max(r_tg["launches"], 1), net=wl.net, tuning=tuning)
     classes = {k: fn.profile_read(k) for k in ("tangent_gemm", "det_tangent", "two_layer", "means", "tanh",
                                                  "value_pass", "adjoint")}
     fn.profile(False)
@@ -694,6 +740,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--check-launch", action="store_true", help="host-only check of the rank launch, then exit")
+    ap.add_argument("--eloc-pass", type=int, default=0, metavar="DIV",
+                    help="run one local-energy pass on the workload's walker counts divided by DIV (after --warmup "
+                         "passes) and exit: the small case for ncu captures of the GEMM class")
+    ap.add_argument("--pass-tuning", default="residual_smem=1",
+                    help="tuning fields for --eloc-pass, e.g. residual_smem=1,layer_groups=2")
     args = ap.parse_args()
     if args.side is None:
         args.side = ("ne,ar,ar@16384,kr,envelope" if args.workload == DEFAULT_WORKLOAD and args.impl == "ours"
@@ -717,6 +768,9 @@ def main():
         if int(os.environ.get("RANK", "0")) != 0:
             return
         run_reference(args, wl)
+        return
+    if args.eloc_pass > 0:
+        run_eloc_pass(args, wl)
         return
     run_gpu(args, wl)
 
