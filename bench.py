@@ -448,11 +448,12 @@ def envelope_overhead(flush, args):
 
 
 def run_eloc_pass(args, wl):
-    """One local-energy pass of the workload with every geometry's walker count
-    divided by --eloc-pass (at least one walker each), after --warmup passes:
-    the small case on which ncu captures the DRAM traffic of the tensor-core
-    GEMM class (only k_tc_gemm launches of local-energy passes run after the
-    context is set up).  Prints the walkers and tuning as one JSON line."""
+    """One local-energy pass (or, with --pass-kind value, one log|psi| pass) of
+    the workload with every geometry's walker count divided by --eloc-pass (at
+    least one walker each), after --warmup passes: the small case on which ncu
+    captures the DRAM traffic of the tensor-core GEMM class (only k_tc_gemm
+    launches of local-energy passes run after the context is set up) or a
+    pass's launch list.  Prints the walkers and tuning as one JSON line."""
     import dataclasses
     import torch
     from paper_2011_07125_gb300 import synth
@@ -467,15 +468,16 @@ def run_eloc_pass(args, wl):
     tuning = {k: int(v) for k, v in tuning.items()}
     if prec == "mixed":
         fn.set_tuning(**tuning)
+    run = (lambda: fn.logpsi(x)) if args.pass_kind == "value" else (lambda: fn.local_energy(x))
     for _ in range(args.warmup):
-        fn.local_energy(x)
+        run()
     torch.cuda.synchronize()
     fn.profile(True)
-    fn.local_energy(x)
+    run()
     torch.cuda.synchronize()
     r = fn.profile_read("tangent_gemm")
     st = fn.sync()
-    print(json.dumps({"eloc_pass": wl.name, "walkers": wl.batch, "counts": wl.counts, "precision": prec,
+    print(json.dumps({"pass": args.pass_kind, "workload": wl.name, "walkers": wl.batch, "counts": wl.counts, "precision": prec,
                       "tuning": tuning, "gemm_class_launches": r["launches"], "gemm_class_ms": r["ms"],
                       "status": st}), flush=True)
     fn.close()
@@ -743,6 +745,8 @@ def main():
     ap.add_argument("--eloc-pass", type=int, default=0, metavar="DIV",
                     help="run one local-energy pass on the workload's walker counts divided by DIV (after --warmup "
                          "passes) and exit: the small case for ncu captures of the GEMM class")
+    ap.add_argument("--pass-kind", default="eloc", choices=["eloc", "value"],
+                    help="with --eloc-pass: the pass to run (local energy, or log|psi| alone)")
     ap.add_argument("--pass-tuning", default="residual_smem=1",
                     help="tuning fields for --eloc-pass, e.g. residual_smem=1,layer_groups=2")
     args = ap.parse_args()

@@ -18,6 +18,7 @@
 // means of its input (the input features h^0_ij).
 #include <mutex>
 
+#include "f32x2.cuh"
 #include "fn_internal.cuh"
 
 namespace fn {
@@ -208,11 +209,12 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_l
 #pragma unroll
       for (int r = 0; r < R; ++r)
         prow[r] = Q == 1 ? min(pq + r * nq, np - 1) * IPS : pq * IPS + r * DIN;
-      float acc[R][8];
+      // accumulators as feature pairs (2j, 2j + 1): packed FMAs
+      f2_t acc2[R][4];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[r][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc2[r][j] = 0ull;
 #pragma unroll
       for (int k = 0; k < DIN; k += 4) {
         float4 xv[R];
@@ -220,17 +222,26 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_l
         for (int r = 0; r < R; ++r) xv[r] = *reinterpret_cast<const float4*>(sin + prow[r] + k);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const float4 w0 = *reinterpret_cast<const float4*>(sW + (k + kk) * DO + fg * 8);
-          const float4 w1 = *reinterpret_cast<const float4*>(sW + (k + kk) * DO + fg * 8 + 4);
-          const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+          const ulonglong2 w0 = *reinterpret_cast<const ulonglong2*>(sW + (k + kk) * DO + fg * 8);
+          const ulonglong2 w1 = *reinterpret_cast<const ulonglong2*>(sW + (k + kk) * DO + fg * 8 + 4);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float xr = comp(xv[r], kk);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[r][j] = fmaf(wv[j], xr, acc[r][j]);
+            const f2_t xr = f2_splat(comp(xv[r], kk));
+            f2_fma(acc2[r][0], w0.x, xr);
+            f2_fma(acc2[r][1], w0.y, xr);
+            f2_fma(acc2[r][2], w1.x, xr);
+            f2_fma(acc2[r][3], w1.y, xr);
           }
         }
       }
+      float acc[R][8];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[r][2 * j] = f2_lo(acc2[r][j]);
+          acc[r][2 * j + 1] = f2_hi(acc2[r][j]);
+        }
       // forward-Laplacian tanh, residual, stores (shared output tile, new rows, tanh values)
       const int npair = Q == 1 ? R : 1;
 #pragma unroll
