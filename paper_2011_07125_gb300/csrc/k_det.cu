@@ -28,16 +28,20 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
                               bool count) {
   T ra[NM], rb[NM];
   const long NSS = a.nss;
-  // determinant only, in FP32: half-warp LU and fast exponentials (the stored
-  // forward of the adjoint keeps the accurate path)
+  // determinant only (isotropic envelope, no stored inverse or envelope): the
+  // envelope from FP32 exponentials in both precisions (the FP64 redo of an
+  // ill-conditioned pair repeats the elimination, not the FP32 inputs), and in
+  // FP32 the half-warp LU; the stored forward of the adjoint keeps the
+  // accurate path
+  const bool fast_env = !a.minv && !a.env && !a.full_env;
   bool fast = false;
-  if constexpr (std::is_same<T, float>::value) fast = !a.minv && !a.env && !a.full_env;
+  if constexpr (std::is_same<T, float>::value) fast = fast_env;
 #pragma unroll
   for (int c = 0; c < NM; ++c) {
     ra[c] = (c == sl) ? T(1) : T(0);
     rb[c] = (c == sl) ? T(1) : T(0);
   }
-  if (fast && sl < m.ns) {
+  if (fast_env && sl < m.ns) {
     // nuclei outer, this lane's columns inner: pi and sigma loaded once per
     // nucleus, exp(-|sigma| d) as 2^(-|sigma| log2(e) d)
     const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
@@ -56,7 +60,7 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
     const int ostride = (int)(a.C * a.ldo);
 #pragma unroll
     for (int c = 0; c < NM; ++c)
-      if (c < m.ns) ra[c] = (T)(ob[c * ostride] * ev[c]);
+      if (c < m.ns) ra[c] = (T)ob[c * ostride] * (T)ev[c];
   } else if (sl < m.ns) {
     const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
     const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + sl) * a.N;
@@ -129,7 +133,7 @@ __device__ __forceinline__ void pair_distances(const DetArgs& a, const MatId& m,
 // k_det_value_pair_redo (kept out of this kernel, whose registers it would
 // otherwise set).
 template <int NM>
-__global__ void __launch_bounds__(128) k_det_value_pair(DetArgs a) {
+__global__ void __launch_bounds__(128, 6) k_det_value_pair(DetArgs a) {
   extern __shared__ float dsh[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = lane >> 4, sl = lane & 15;
