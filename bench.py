@@ -448,7 +448,8 @@ def envelope_overhead(flush, args):
 
 
 def run_eloc_pass(args, wl):
-    """One local-energy pass (or, with --pass-kind value, one log|psi| pass) of
+    """One local-energy pass (with --pass-kind value one log|psi| pass, with
+    --pass-kind grad a local-energy pass and the VMC gradient) of
     the workload with every geometry's walker count divided by --eloc-pass (at
     least one walker each), after --warmup passes: the small case on which ncu
     captures the DRAM traffic of the tensor-core GEMM class (only k_tc_gemm
@@ -468,7 +469,13 @@ def run_eloc_pass(args, wl):
     tuning = {k: int(v) for k, v in tuning.items()}
     if prec == "mixed":
         fn.set_tuning(**tuning)
-    run = (lambda: fn.logpsi(x)) if args.pass_kind == "value" else (lambda: fn.local_energy(x))
+    def run():
+        if args.pass_kind == "value":
+            fn.logpsi(x)
+        elif args.pass_kind == "grad":
+            fn.energy_grad(x, fn.local_energy(x)["eloc"])
+        else:
+            fn.local_energy(x)
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
@@ -745,8 +752,9 @@ def main():
     ap.add_argument("--eloc-pass", type=int, default=0, metavar="DIV",
                     help="run one local-energy pass on the workload's walker counts divided by DIV (after --warmup "
                          "passes) and exit: the small case for ncu captures of the GEMM class")
-    ap.add_argument("--pass-kind", default="eloc", choices=["eloc", "value"],
-                    help="with --eloc-pass: the pass to run (local energy, or log|psi| alone)")
+    ap.add_argument("--pass-kind", default="eloc", choices=["eloc", "value", "grad"],
+                    help="with --eloc-pass: the pass to run (local energy, log|psi| alone, or local energy and "
+                         "the VMC gradient)")
     ap.add_argument("--pass-tuning", default="residual_smem=1",
                     help="tuning fields for --eloc-pass, e.g. residual_smem=1,layer_groups=2")
     args = ap.parse_args()
