@@ -379,6 +379,7 @@ void forward(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, bool tangen
     pa.mhi = mhi;
     pa.mlo = mlo;
     pa.ldm = m2_ld(l + 1);
+    pa.mma = c->prec == FN_PREC_MIXED ? 1 : 0;
     if (!launch_pair_layer(s, pa, din2_of(t, l), d2, Q)) c->host_fail = true;
   };
   launch_features(s, x, Bc, w0, n, N, C, Q, g, H0, E0);

@@ -153,6 +153,8 @@ struct PairArgs {
   __nv_bfloat16* mhi;   //   as BF16 hi / lo (lo may be null); columns 2 dout .. ldm-1 zero
   __nv_bfloat16* mlo;
   long ldm;
+  int mma;              // 32 -> 32 layers of a value pass (Q = 1): the contraction on warp
+                        // MMAs with BF16 hi + lo operands (three products, FP32 accumulation)
   int tg;               // set by the launcher
 };
 bool pair_layer_supported(int n, int din, int dout, bool layer, int Q, int C, long ldm);

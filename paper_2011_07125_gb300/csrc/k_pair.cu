@@ -51,8 +51,27 @@ constexpr int out_stride() { return Q * DO + 4; }
 template <int Q>
 constexpr int task_rows() { return Q == 1 ? 4 : Q; }
 // Resident blocks per SM the kernel is built for (registers and shared memory).
-template <int Q, bool LAYER>
-constexpr int min_blocks() { return LAYER ? (Q == 1 ? 3 : 2) : 4; }
+template <int Q, bool LAYER, bool MMA = false>
+constexpr int min_blocks() { return MMA ? 2 : (LAYER ? (Q == 1 ? 3 : 2) : 4); }
+
+// D += A B for one m16n8k16 BF16 tile (A row-major 16 x 16, B column-major
+// 16 x 8), FP32 accumulation.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Two FP32 values as packed BF16 hi (x0 in the low half) and the packed
+// BF16 remainders.
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
 
 template <int DIN, int DO, int Q, bool LAYER>
 size_t pair_smem_bytes(int n, int tg) {
@@ -154,9 +173,10 @@ __device__ __forceinline__ void spin_sums(const PairArgs& a, int tge, const floa
   }
 }
 
-template <int DIN, int DO, int Q, bool LAYER>
-__global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_layer(PairArgs a) {
+template <int DIN, int DO, int Q, bool LAYER, bool MMA>
+__global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_pair_layer(PairArgs a) {
   static_assert(DIN % 4 == 0 && (DO % 8 == 0 || !LAYER), "feature counts");
+  static_assert(!MMA || (LAYER && DIN == 32 && DO == 32), "warp-MMA contraction: 32 -> 32 layers");
   constexpr int IPS = in_stride<DIN, Q>();
   constexpr int OPS = LAYER ? out_stride<DO, Q>() : IPS;
   constexpr int ORS = LAYER ? DO : DIN;  // row stride of one quantity in the output tile
@@ -178,6 +198,22 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_l
       sW[t] = a.W[f * DIN + k];
     }
     for (int t = tid; t < DO; t += kPairThreads) sb[t] = a.cb[t];
+  }
+  // warp-MMA contraction: W^T as the B operand (k = input feature, n = output
+  // feature), fragments for two k-steps and four column tiles, split hi + lo
+  const int lane = tid & 31, warp = tid >> 5, fgr = lane >> 2, fq = lane & 3;
+  uint32_t wbh[MMA ? 2 : 1][MMA ? 4 : 1][2], wbl[MMA ? 2 : 1][MMA ? 4 : 1][2];
+  if constexpr (MMA) {
+    __syncthreads();  // sW is complete
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = ks * 16 + 2 * fq + 8 * h, f = nt * 8 + fgr;
+          split_bf16x2(sW[k * DO + f], sW[(k + 1) * DO + f], wbh[ks][nt][h], wbl[ks][nt][h]);
+        }
   }
   const float inv0 = a.n_up > 0 ? 1.f / (float)a.n_up : 0.f;
   const float inv1 = n - a.n_up > 0 ? 1.f / (float)(n - a.n_up) : 0.f;
@@ -201,6 +237,96 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_l
       dense_means<Q, ORS, OPS>(a, g0, tge, cur, sS, inv0, inv1);
       continue;
     }
+    if constexpr (MMA) {
+      // ---- the layer on warp MMAs: pre-activations of 16-row strips (row
+      // p Q + q is quantity q of pair p) into the output tile, then the
+      // forward-Laplacian tanh rule per (pair, 8 features) in place ----
+      const int rows = np * Q;
+      for (int st = warp; st * 16 < rows; st += kPairThreads / 32) {
+        const int r0 = st * 16 + fgr, r1 = r0 + 8;
+        const float* x0 = r0 < rows ? sin + (r0 / Q) * IPS + (r0 % Q) * DIN : nullptr;
+        const float* x1 = r1 < rows ? sin + (r1 / Q) * IPS + (r1 % Q) * DIN : nullptr;
+        float acc[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[nt][r] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          uint32_t ah[4], al[4];
+          const int k = ks * 16 + 2 * fq;
+          const float2 v00 = x0 ? *reinterpret_cast<const float2*>(x0 + k) : make_float2(0.f, 0.f);
+          const float2 v10 = x1 ? *reinterpret_cast<const float2*>(x1 + k) : make_float2(0.f, 0.f);
+          const float2 v01 = x0 ? *reinterpret_cast<const float2*>(x0 + k + 8) : make_float2(0.f, 0.f);
+          const float2 v11 = x1 ? *reinterpret_cast<const float2*>(x1 + k + 8) : make_float2(0.f, 0.f);
+          split_bf16x2(v00.x, v00.y, ah[0], al[0]);
+          split_bf16x2(v10.x, v10.y, ah[1], al[1]);
+          split_bf16x2(v01.x, v01.y, ah[2], al[2]);
+          split_bf16x2(v11.x, v11.y, ah[3], al[3]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            mma_bf16_16816(acc[nt], al, wbh[ks][nt][0], wbh[ks][nt][1]);
+            mma_bf16_16816(acc[nt], ah, wbl[ks][nt][0], wbl[ks][nt][1]);
+            mma_bf16_16816(acc[nt], ah, wbh[ks][nt][0], wbh[ks][nt][1]);
+          }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int f = nt * 8 + 2 * fq;
+          if (r0 < rows)
+            *reinterpret_cast<float2*>(sout_l + (r0 / Q) * OPS + (r0 % Q) * DO + f) = make_float2(acc[nt][0], acc[nt][1]);
+          if (r1 < rows)
+            *reinterpret_cast<float2*>(sout_l + (r1 / Q) * OPS + (r1 % Q) * DO + f) = make_float2(acc[nt][2], acc[nt][3]);
+        }
+      }
+      __syncthreads();  // every pre-activation of the tile is in the output tile
+      for (int task = tid; task < np * FG; task += kPairThreads) {
+        const int p = task / FG, fg = task - p * FG;
+        const float* ip = sin + p * IPS;
+        float* op = sout_l + p * OPS;
+        float zq[Q][8], ov[Q][8], yv[8];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const float4 z0 = *reinterpret_cast<const float4*>(op + q * DO + fg * 8);
+          const float4 z1 = *reinterpret_cast<const float4*>(op + q * DO + fg * 8 + 4);
+          zq[q][0] = z0.x; zq[q][1] = z0.y; zq[q][2] = z0.z; zq[q][3] = z0.w;
+          zq[q][4] = z1.x; zq[q][5] = z1.y; zq[q][6] = z1.z; zq[q][7] = z1.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int f = fg * 8 + j;
+          const float y = tanhf(zq[0][j] + sb[f]);
+          const float s = 1.f - y * y;
+          yv[j] = y;
+          ov[0][j] = y + (a.residual ? ip[f] : 0.f);
+          if (Q > 1) {
+            const float sq = zq[1][j] * zq[1][j] + zq[2][j] * zq[2][j] + zq[3][j] * zq[3][j];
+#pragma unroll
+            for (int q = 1; q <= 3 && q < Q; ++q) ov[q][j] = s * zq[q][j] + (a.residual ? ip[q * DIN + f] : 0.f);
+            if (Q > 4) ov[4][j] = s * zq[4][j] - 4.f * y * s * sq + (a.residual ? ip[4 * DIN + f] : 0.f);
+          }
+        }
+        const long gp = g0 * n + p;  // global pair index
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const float4 o0 = make_float4(ov[q][0], ov[q][1], ov[q][2], ov[q][3]);
+          const float4 o1 = make_float4(ov[q][4], ov[q][5], ov[q][6], ov[q][7]);
+          float* so = op + q * DO + fg * 8;
+          *reinterpret_cast<float4*>(so) = o0;
+          *reinterpret_cast<float4*>(so + 4) = o1;
+          if (a.Eout) {
+            float* go = a.Eout + (gp * Q + q) * DO + fg * 8;
+            *reinterpret_cast<float4*>(go) = o0;
+            *reinterpret_cast<float4*>(go + 4) = o1;
+          }
+        }
+        if (a.Y2) {
+          float* gy = a.Y2 + gp * DO + fg * 8;
+          *reinterpret_cast<float4*>(gy) = make_float4(yv[0], yv[1], yv[2], yv[3]);
+          *reinterpret_cast<float4*>(gy + 4) = make_float4(yv[4], yv[5], yv[6], yv[7]);
+        }
+      }
+    } else {
     // ---- the layer: R rows x 8 features per task ----
     const int nq = Q == 1 ? (np + 3) / 4 : np;  // tasks per feature group
     for (int task = tid; task < nq * FG; task += kPairThreads) {
@@ -286,6 +412,7 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_l
         }
       }
     }
+    }  // SIMT contraction
     __syncthreads();  // output tile complete; the input tile is free
     if (next < n_tiles) load_tile<DIN, Q>(a.Ein, next * tg, (int)min((long)tg, a.groups - next * tg), n, sin);
     spin_sums<Q, ORS, OPS>(a, tge, sout_l, sS);
@@ -295,10 +422,10 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER>()) k_pair_l
   cp_async_wait_all();  // no copy outlives the block
 }
 
-template <int DIN, int DO, int Q, bool LAYER>
+template <int DIN, int DO, int Q, bool LAYER, bool MMA = false>
 void launch_inst(cudaStream_t s, PairArgs a) {
-  auto kern = k_pair_layer<DIN, DO, Q, LAYER>;
-  constexpr int MB = min_blocks<Q, LAYER>();
+  auto kern = k_pair_layer<DIN, DO, Q, LAYER, MMA>;
+  constexpr int MB = min_blocks<Q, LAYER, MMA>();
   const size_t budget = kSmemPerSM / MB - 1024;
   static PerDeviceOnce attr;  // the attribute is per function and device
   attr([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget); });
@@ -337,7 +464,12 @@ bool dispatch(cudaStream_t s, const PairArgs& a, int din, int dout) {
   if (din == 4 && dout == 16) return launch_inst<4, 16, Q, true>(s, a), true;
   if (din == 16 && dout == 16) return launch_inst<16, 16, Q, true>(s, a), true;
   if (din == 4 && dout == 32) return launch_inst<4, 32, Q, true>(s, a), true;
-  if (din == 32 && dout == 32) return launch_inst<32, 32, Q, true>(s, a), true;
+  if (din == 32 && dout == 32) {
+    // value rows only: in the local-energy pass (Q = 5) the contraction is a
+    // small share of the layer, which keeps its FP32 FMAs
+    if (Q == 1 && a.mma) return launch_inst<32, 32, 1, true, true>(s, a), true;
+    return launch_inst<32, 32, Q, true>(s, a), true;
+  }
   return false;
 }
 

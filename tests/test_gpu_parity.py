@@ -14,8 +14,8 @@ import pytest
 
 import oracle
 from paper_2011_07125_gb300 import synth
-from helpers import (TOL_ELOC_ABS, TOL_LOGPSI_REL, U32, conditioning, gamma, eloc_bound, emean_bound, equilibrated,
-                     logpsi_bound, rel_err, setup)
+from helpers import (TOL_ELOC_ABS, TOL_LOGPSI_REL, U32, U_MIXED, conditioning, gamma, eloc_bound, emean_bound,
+                     equilibrated, logpsi_bound, rel_err, setup)
 
 TOL_GRAD_FP32 = 1e-3
 
@@ -320,8 +320,13 @@ def test_step_graph_matches_calls(name, per, prec):
                                            ("c4h4x8", 2, "mixed")])
 def test_pair_fused_matches_separate(name, per, prec):
     """The fused two-electron layer + spin-mean kernel against the separate
-    kernels: same arithmetic in the same order, on the value pass, the
-    local-energy pass and the adjoint (whose forward stores every layer)."""
+    kernels on the value pass, the local-energy pass and the adjoint (whose
+    forward stores every layer).  Same arithmetic in the same order, except
+    the value rows of 32 -> 32 layers in the mixed path: the fused kernel
+    contracts them on warp MMAs with BF16 hi + lo operands (about 16
+    significant bits), the separate kernel in FP32; there both log|psi| stay
+    within the mixed log|psi| bar of the oracle and the gradients agree to
+    1e-3 (the mixed gradient bar is 1e-2)."""
     wl, lay, P, x, geo = setup(name, per)
     fn = make(wl, P, precision=prec)
     xx = cuda(x)
@@ -335,10 +340,18 @@ def test_pair_fused_matches_separate(name, per, prec):
         res.append((lp, out["eloc"], out["logpsi"], g))
         assert fn.sync() == "FN_OK"
     (lp0, e0, l0, g0), (lp1, e1, l1, g1) = res
-    torch.testing.assert_close(lp0, lp1, rtol=1e-6, atol=1e-6)
     torch.testing.assert_close(l0, l1, rtol=1e-6, atol=1e-6)
     torch.testing.assert_close(e0, e1, rtol=1e-4, atol=1e-4)
-    assert float((g0 - g1).norm() / g1.norm()) < 1e-5
+    if prec == "fp32":
+        torch.testing.assert_close(lp0, lp1, rtol=1e-6, atol=1e-6)
+        assert float((g0 - g1).norm() / g1.norm()) < 1e-5
+    else:
+        ref = oracle.local_energy(wl.net, P, wl.geoms, x, geo=geo)
+        bound = logpsi_bound(wl.net, ref, u=U_MIXED)
+        for lp in (lp0, lp1):
+            assert np.all(np.abs(lp.cpu().numpy() - ref["logpsi"]) <= bound)
+        assert np.all(np.abs((lp0 - lp1).cpu().numpy()) <= bound)
+        assert float((g0 - g1).norm() / g1.norm()) < 1e-3
     print(name, prec, "fused vs separate: max |dE|", float((e0 - e1).abs().max()),
           "bitwise" if torch.equal(e0, e1) and torch.equal(lp0, lp1) else "not bitwise")
 
