@@ -1005,6 +1005,7 @@ void vjp_chunk_tc(fn_ctx* c, Arena& ar, const float* x, long Bc, long w0, const 
       pb.grad_W = grad + Lo.W[l];
       pb.grad_c = grad + Lo.c[l];
       pb.partial = pb_scr;
+      pb.mma = 1;  // the tensor-core adjoint (mixed path)
       fail_if(launch_pair_bwd(s, pb, a2, d2));
     } else if (l < L - 1) {
       launch_tanh_bwd(s, Enext, st.Y2[l], pairs, d2, Z2bar);

@@ -177,6 +177,8 @@ struct PairBwdArgs {
   double* grad_W;         // [dout][din]
   double* grad_c;         // [dout]
   float* partial;         // scratch: pair_bwd_scratch_floats(din, dout) floats
+  int mma;                // 32 -> 32 layers: dW and Ein_bar on warp MMAs with BF16 hi + lo
+                          // operands (three products, FP32 accumulation)
 };
 bool pair_bwd_supported(int din, int dout);
 long pair_bwd_scratch_floats(int din, int dout);

@@ -582,6 +582,143 @@ __global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
   }
 }
 
+// Mixed-path variant for 32 -> 32 layers: the staging, Zbar and dc as in
+// k_pair_bwd; dW = Zbar^T Ein (M = output feature, N = input feature, K =
+// the tile's pairs) and Ein_bar = Zbar W (M = pair, N = input feature, K =
+// output feature) on m16n8k16 warp MMAs with BF16 hi + lo operands (three
+// products, FP32 accumulation).  Warp w owns the dW block of rows 16 (w / 4)
+// and columns 8 (w % 4); the Ein_bar blocks of a tile go round the warps.
+// Fragments (g = lane / 4, q = lane % 4): A rows g, g + 8 and columns 2q,
+// 2q + 1 (+ 8); B rows 2q, 2q + 1 (+ 8) and column g; the result rows g, g + 8
+// and columns 2q, 2q + 1.
+template <int DIN, int DO>
+__global__ void __launch_bounds__(256) k_pair_bwd_mma(PairBwdArgs a) {
+  static_assert(DIN == 32 && DO == 32, "warp-MMA pair backward: 32 -> 32 layers");
+  constexpr int P = kBwdPairs, ZS = DO + 1, ES = DIN + 4;
+  static_assert(P % 16 == 0, "whole 16-pair steps");
+  __shared__ float Zt[P * ZS];
+  __shared__ float Ot[P * ZS];
+  __shared__ __align__(16) float Et[P * ES];
+  __shared__ __align__(16) float Ws[DO * DIN];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, q = lane & 3;
+  for (int t = tid; t < DO * DIN; t += 256) Ws[t] = a.W[t];
+  __syncthreads();
+  // W as the B operand of Ein_bar (k = output feature f, n = input feature)
+  uint32_t wbh[2][4][2], wbl[2][4][2];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int f = ks * 16 + 2 * q + 8 * h, k = nt * 8 + g;
+        split_bf16x2(Ws[f * DIN + k], Ws[(f + 1) * DIN + k], wbh[ks][nt][h], wbl[ks][nt][h]);
+      }
+  const int mt = warp >> 2, nt0 = warp & 3;
+  float dacc[4] = {0.f, 0.f, 0.f, 0.f}, cacc = 0.f;
+  const long n_tiles = (a.pairs + P - 1) / P;
+  for (long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long p0 = tile * P;
+    const int np = (int)min((long)P, a.pairs - p0);
+    __syncthreads();  // previous tile fully used
+    for (int t = tid; t < P * (DO / 4); t += 256) {
+      const int p = t / (DO / 4), qq = (t % (DO / 4)) * 4;
+      float* zr = Zt + p * ZS + qq;
+      float* orr = Ot + p * ZS + qq;
+      if (p >= np) {  // rows past the tile's pairs add nothing to the MMAs
+        zr[0] = zr[1] = zr[2] = zr[3] = 0.f;
+        orr[0] = orr[1] = orr[2] = orr[3] = 0.f;
+        continue;
+      }
+      float4 ob = a.Eout_bar ? *reinterpret_cast<const float4*>(a.Eout_bar + (p0 + p) * DO + qq)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.M2bar) {
+        const long gp = p0 + p, wi = gp / a.n;
+        const int j = (int)(gp - wi * a.n), sj = j < a.n_up ? 0 : 1;
+        const float ns = (float)(sj == 0 ? a.n_up : a.n - a.n_up);
+        const float4 m = *reinterpret_cast<const float4*>(a.M2bar + wi * 2 * DO + sj * DO + qq);
+        ob.x += m.x / ns;
+        ob.y += m.y / ns;
+        ob.z += m.z / ns;
+        ob.w += m.w / ns;
+      }
+      const float4 y = *reinterpret_cast<const float4*>(a.Y + (p0 + p) * DO + qq);
+      zr[0] = ob.x * (1.f - y.x * y.x);
+      zr[1] = ob.y * (1.f - y.y * y.y);
+      zr[2] = ob.z * (1.f - y.z * y.z);
+      zr[3] = ob.w * (1.f - y.w * y.w);
+      orr[0] = ob.x;
+      orr[1] = ob.y;
+      orr[2] = ob.z;
+      orr[3] = ob.w;
+    }
+    for (int t = tid; t < P * (DIN / 4); t += 256) {
+      const int p = t / (DIN / 4), qq = (t % (DIN / 4)) * 4;
+      *reinterpret_cast<float4*>(Et + p * ES + qq) =
+          p < np ? *reinterpret_cast<const float4*>(a.Ein + (p0 + p) * DIN + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (tid < DO)
+      for (int p = 0; p < np; ++p) cacc += Zt[p * ZS + tid];
+    // dW block (rows 16 mt, columns 8 nt0) over the tile's pairs
+#pragma unroll 2
+    for (int ks = 0; ks < P / 16; ++ks) {
+      const int pa = ks * 16 + 2 * q, f0 = mt * 16 + g, k0 = nt0 * 8 + g;
+      uint32_t ah[4], al[4], bh[2], bl[2];
+      split_bf16x2(Zt[pa * ZS + f0], Zt[(pa + 1) * ZS + f0], ah[0], al[0]);
+      split_bf16x2(Zt[pa * ZS + f0 + 8], Zt[(pa + 1) * ZS + f0 + 8], ah[1], al[1]);
+      split_bf16x2(Zt[(pa + 8) * ZS + f0], Zt[(pa + 9) * ZS + f0], ah[2], al[2]);
+      split_bf16x2(Zt[(pa + 8) * ZS + f0 + 8], Zt[(pa + 9) * ZS + f0 + 8], ah[3], al[3]);
+      split_bf16x2(Et[pa * ES + k0], Et[(pa + 1) * ES + k0], bh[0], bl[0]);
+      split_bf16x2(Et[(pa + 8) * ES + k0], Et[(pa + 9) * ES + k0], bh[1], bl[1]);
+      mma_bf16_16816(dacc, al, bh[0], bh[1]);
+      mma_bf16_16816(dacc, ah, bl[0], bl[1]);
+      mma_bf16_16816(dacc, ah, bh[0], bh[1]);
+    }
+    if (a.Ein_bar) {
+      for (int blk = warp; blk < (P / 16) * 4; blk += 8) {
+        const int pm = blk >> 2, nt = blk & 3, pr = pm * 16 + g;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const int fa = ks * 16 + 2 * q;
+          uint32_t ah[4], al[4];
+          split_bf16x2(Zt[pr * ZS + fa], Zt[pr * ZS + fa + 1], ah[0], al[0]);
+          split_bf16x2(Zt[(pr + 8) * ZS + fa], Zt[(pr + 8) * ZS + fa + 1], ah[1], al[1]);
+          split_bf16x2(Zt[pr * ZS + fa + 8], Zt[pr * ZS + fa + 9], ah[2], al[2]);
+          split_bf16x2(Zt[(pr + 8) * ZS + fa + 8], Zt[(pr + 8) * ZS + fa + 9], ah[3], al[3]);
+          mma_bf16_16816(acc, al, wbh[ks][nt][0], wbh[ks][nt][1]);
+          mma_bf16_16816(acc, ah, wbl[ks][nt][0], wbl[ks][nt][1]);
+          mma_bf16_16816(acc, ah, wbh[ks][nt][0], wbh[ks][nt][1]);
+        }
+        const int k = nt * 8 + 2 * q;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int p = pr + 8 * h;
+          if (p >= np) continue;
+          float o0 = acc[2 * h], o1 = acc[2 * h + 1];
+          if (a.residual) {
+            o0 += Ot[p * ZS + k];
+            o1 += Ot[p * ZS + k + 1];
+          }
+          *reinterpret_cast<float2*>(a.Ein_bar + (p0 + p) * DIN + k) = make_float2(o0, o1);
+        }
+      }
+    }
+  }
+  // this block's partial sums, laid out as in k_pair_bwd
+  constexpr int PS = DO * DIN + DO;
+  float* part = a.partial + (long)blockIdx.x * PS;
+  {
+    const int f = mt * 16 + g, k = nt0 * 8 + 2 * q;
+    part[f * DIN + k] = dacc[0];
+    part[f * DIN + k + 1] = dacc[1];
+    part[(f + 8) * DIN + k] = dacc[2];
+    part[(f + 8) * DIN + k + 1] = dacc[3];
+  }
+  if (tid < DO) part[DO * DIN + tid] = cacc;
+}
+
 // grad[j] += sum over blocks of the partials, in FP64 and block order.
 __global__ void k_pair_bwd_reduce(const float* __restrict__ part, int nblocks, int ps, int nw, double* grad_W,
                                   double* grad_c) {
@@ -593,17 +730,18 @@ __global__ void k_pair_bwd_reduce(const float* __restrict__ part, int nblocks, i
   else grad_c[j - nw] += s;
 }
 
-template <int DIN, int DO>
+template <int DIN, int DO, bool MMA = false>
 void launch_bwd_inst(cudaStream_t s, const PairBwdArgs& a) {
   int occ = 0, dev = 0, sms = 152;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_bwd<DIN, DO>, 256, 0) != cudaSuccess || occ < 1)
+  auto kern = MMA ? k_pair_bwd_mma<32, 32> : k_pair_bwd<DIN, DO>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1)
     occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long tiles = (a.pairs + kBwdPairs - 1) / kBwdPairs;
   long blocks = std::min<long>(tiles, (long)sms * occ);
   if (blocks > kBwdMaxBlocks) blocks = kBwdMaxBlocks;
-  FN_COUNT(1), k_pair_bwd<DIN, DO><<<(unsigned)blocks, 256, 0, s>>>(a);
+  FN_COUNT(1), kern<<<(unsigned)blocks, 256, 0, s>>>(a);
   const int ps = DO * DIN + DO;
   FN_COUNT(1), k_pair_bwd_reduce<<<(ps + 255) / 256, 256, 0, s>>>(a.partial, (int)blocks, ps, DO * DIN, a.grad_W,
                                                                    a.grad_c);
@@ -624,7 +762,10 @@ bool launch_pair_bwd(cudaStream_t s, const PairBwdArgs& a, int din, int dout) {
   if (din == 4 && dout == 16) return launch_bwd_inst<4, 16>(s, a), true;
   if (din == 16 && dout == 16) return launch_bwd_inst<16, 16>(s, a), true;
   if (din == 4 && dout == 32) return launch_bwd_inst<4, 32>(s, a), true;
-  if (din == 32 && dout == 32) return launch_bwd_inst<32, 32>(s, a), true;
+  if (din == 32 && dout == 32) {
+    if (a.mma) return launch_bwd_inst<32, 32, true>(s, a), true;
+    return launch_bwd_inst<32, 32>(s, a), true;
+  }
   return false;
 }
 
