@@ -100,10 +100,19 @@ __global__ void k_colsum_part(const float* __restrict__ X, long rows, long cols,
   const long c = (long)blockIdx.x * 32 + tx;
   const long r0 = (long)blockIdx.y * rpc;
   const long r1 = min(rows, r0 + rpc);
-  // FP32 over this thread's rows (a few hundred), FP64 from here on
+  // FP32 over this thread's rows (a few hundred) in eight interleaved partial
+  // sums (eight loads in flight), FP64 from here on
   float s = 0.f;
-  if (c < cols)
-    for (long r = r0 + ty; r < r1; r += 8) s += X[r * ldx + c];
+  if (c < cols) {
+    float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    long r = r0 + ty;
+    for (; r + 56 < r1; r += 64) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) p[u] += X[(r + 8 * u) * ldx + c];
+    }
+    for (; r < r1; r += 8) p[0] += X[r * ldx + c];
+    s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+  }
   sh[ty][tx] = (double)s;
   __syncthreads();
   if (ty == 0 && c < cols) {
@@ -166,6 +175,45 @@ __global__ void k_spread_mean2(const float* __restrict__ m2bar, long Bc, int n, 
   ebar[idx] += m2bar[wi * 2 * din2 + s * din2 + f] / (float)ns;
 }
 
+// Four elements per thread (16-byte loads and stores) for the elementwise
+// kernels below when the sizes and pointers allow it.
+__global__ void k_tanh_bwd4(const float4* __restrict__ hbar, const float4* __restrict__ Y, long tot4,
+                            float4* __restrict__ zbar) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tot4) return;
+  const float4 y = Y[i], h = hbar[i];
+  zbar[i] = make_float4(h.x * (1.f - y.x * y.x), h.y * (1.f - y.y * y.y), h.z * (1.f - y.z * y.z),
+                        h.w * (1.f - y.w * y.w));
+}
+
+__global__ void k_spread_mean1_4(const float* __restrict__ m1bar, long Bc, int n, int n_up, int din,
+                                 float* __restrict__ hbar) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int d4 = din >> 2;
+  if (idx >= Bc * n * d4) return;
+  const int f = (int)(idx % d4) * 4;
+  const long wi = idx / d4;
+  const int i = (int)(wi % n);
+  const long w = wi / n;
+  const int s = i < n_up ? 0 : 1;
+  const float ns = (float)(s == 0 ? n_up : n - n_up);
+  const float4 m = *reinterpret_cast<const float4*>(m1bar + w * 2 * din + s * din + f);
+  float4* h = reinterpret_cast<float4*>(hbar + wi * din + f);
+  float4 v = *h;
+  v.x += m.x / ns;
+  v.y += m.y / ns;
+  v.z += m.z / ns;
+  v.w += m.w / ns;
+  *h = v;
+}
+
+__global__ void k_add4(float4* __restrict__ dst, const float4* __restrict__ src, long n4) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const float4 a = dst[i], b = src[i];
+  dst[i] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
 __global__ void k_add(float* __restrict__ dst, const float* __restrict__ src, long n) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] += src[i];
@@ -202,7 +250,14 @@ void launch_colsum_accum(cudaStream_t s, const float* X, long rows, long cols, l
 
 void launch_tanh_bwd(cudaStream_t s, const float* hbar, const float* Y, long rows, int d, float* zbar) {
   long tot = rows * d;
-  if (tot > 0) FN_COUNT(1), k_tanh_bwd<<<nblk(tot, 256), 256, 0, s>>>(hbar, Y, tot, zbar);
+  if (tot <= 0) return;
+  if (tot % 4 == 0 && ((uintptr_t)hbar | (uintptr_t)Y | (uintptr_t)zbar) % 16 == 0) {
+    FN_COUNT(1), k_tanh_bwd4<<<nblk(tot / 4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(hbar),
+                                                               reinterpret_cast<const float4*>(Y), tot / 4,
+                                                               reinterpret_cast<float4*>(zbar));
+    return;
+  }
+  FN_COUNT(1), k_tanh_bwd<<<nblk(tot, 256), 256, 0, s>>>(hbar, Y, tot, zbar);
 }
 
 void launch_walker_sum(cudaStream_t s, const float* X, long Bc, int n, int d, float* S) {
@@ -212,7 +267,12 @@ void launch_walker_sum(cudaStream_t s, const float* X, long Bc, int n, int d, fl
 
 void launch_spread_mean1(cudaStream_t s, const float* m1bar, long Bc, int n, int n_up, int din, float* hbar) {
   long tot = Bc * n * din;
-  if (tot > 0) FN_COUNT(1), k_spread_mean1<<<nblk(tot, 256), 256, 0, s>>>(m1bar, Bc, n, n_up, din, hbar);
+  if (tot <= 0) return;
+  if (din % 4 == 0 && ((uintptr_t)m1bar | (uintptr_t)hbar) % 16 == 0) {
+    FN_COUNT(1), k_spread_mean1_4<<<nblk(tot / 4, 256), 256, 0, s>>>(m1bar, Bc, n, n_up, din, hbar);
+    return;
+  }
+  FN_COUNT(1), k_spread_mean1<<<nblk(tot, 256), 256, 0, s>>>(m1bar, Bc, n, n_up, din, hbar);
 }
 
 void launch_spread_mean2(cudaStream_t s, const float* m2bar, long Bc, int n, int n_up, int din2, float* ebar) {
@@ -221,7 +281,13 @@ void launch_spread_mean2(cudaStream_t s, const float* m2bar, long Bc, int n, int
 }
 
 void launch_add(cudaStream_t s, float* dst, const float* src, long n) {
-  if (n > 0) FN_COUNT(1), k_add<<<nblk(n, 256), 256, 0, s>>>(dst, src, n);
+  if (n <= 0) return;
+  if (n % 4 == 0 && ((uintptr_t)dst | (uintptr_t)src) % 16 == 0) {
+    FN_COUNT(1), k_add4<<<nblk(n / 4, 256), 256, 0, s>>>(reinterpret_cast<float4*>(dst),
+                                                        reinterpret_cast<const float4*>(src), n / 4);
+    return;
+  }
+  FN_COUNT(1), k_add<<<nblk(n, 256), 256, 0, s>>>(dst, src, n);
 }
 
 }  // namespace fn
