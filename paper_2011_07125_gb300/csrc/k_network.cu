@@ -48,6 +48,56 @@ __global__ void k_feat1(const float* __restrict__ x, long Bc, long w0, int n, in
   }
 }
 
+// The same rows staged per warp in shared memory (32 rows of 4N floats,
+// stride 4N + 4) and written out as contiguous 16-byte stores: a warp's rows
+// are adjacent in H0, so its stores cover one contiguous range.
+__global__ void __launch_bounds__(128) k_feat1_staged(const float* __restrict__ x, long Bc, long w0, int n, int N,
+                                                      int C, Geo g, float* __restrict__ H0) {
+  extern __shared__ __align__(16) float fsh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int RS = 4 * N + 4;
+  float* wsh = fsh + warp * 32 * RS;
+  const long tot = Bc * n * C;
+  const long r0 = ((long)blockIdx.x * 4 + warp) * 32;
+  if (r0 >= tot) return;  // warp-uniform
+  const int nr = (int)min(32L, tot - r0);
+  const long idx = r0 + lane;
+  if (lane < nr) {
+    const int c = (int)(idx % C);
+    const long wi = idx / C;
+    const int i = (int)(wi % n);
+    const long w = wi / n;
+    const float* R = g.R + (long)geo_of(g, w0 + w) * N * 3;
+    const float* xi = x + (w * n + i) * 3;
+    float* out = wsh + lane * RS;
+    const int n3 = 3 * n;
+    for (int I = 0; I < N; ++I) {
+      float d0 = xi[0] - R[3 * I], d1 = xi[1] - R[3 * I + 1], d2 = xi[2] - R[3 * I + 2];
+      float r = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c == 0) {
+        v[0] = d0; v[1] = d1; v[2] = d2; v[3] = r;
+      } else if (c <= n3) {
+        int e = (c - 1) / 3, dd = (c - 1) % 3;
+        if (e == i) {
+          v[dd] = 1.f;
+          float dv = dd == 0 ? d0 : (dd == 1 ? d1 : d2);
+          v[3] = r > 0.f ? dv / r : 0.f;
+        }
+      } else if (c == n3 + 1) {
+        v[3] = r > 0.f ? 2.f / r : 0.f;
+      }
+      *reinterpret_cast<float4*>(out + 4 * I) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+  __syncwarp();
+  float4* dst = reinterpret_cast<float4*>(H0 + r0 * 4 * N);
+  for (int k = lane; k < nr * N; k += 32) {
+    const int row = k / N, I = k - row * N;
+    dst[k] = *reinterpret_cast<const float4*>(wsh + row * RS + 4 * I);
+  }
+}
+
 // h^0_ij = [r_i - r_j, |r_i - r_j|]; Q = 5 rows (value, d/dr_i xyz, full
 // Laplacian = 2 * (2 / r) for the distance) or Q = 1.  Zero for i = j.
 __global__ void k_feat2(const float* __restrict__ x, long Bc, int n, int Q, float* __restrict__ E0) {
@@ -380,7 +430,11 @@ inline unsigned nblk(long tot, int bs) { return (unsigned)((tot + bs - 1) / bs);
 void launch_features(cudaStream_t s, const float* x, long Bc, long w0, int n, int N, int C, int Q, Geo g, float* H0,
                      float* E0) {
   long t1 = Bc * n * C;
-  if (t1 > 0) FN_COUNT(1), k_feat1<<<nblk(t1, 256), 256, 0, s>>>(x, Bc, w0, n, N, C, g, H0);
+  const size_t fsm = sizeof(float) * 4 * 32 * (4 * N + 4);
+  if (t1 > 0 && fsm <= 48 * 1024 && (uintptr_t)H0 % 16 == 0)
+    FN_COUNT(1), k_feat1_staged<<<(unsigned)((t1 + 127) / 128), 128, fsm, s>>>(x, Bc, w0, n, N, C, g, H0);
+  else if (t1 > 0)
+    FN_COUNT(1), k_feat1<<<nblk(t1, 256), 256, 0, s>>>(x, Bc, w0, n, N, C, g, H0);
   long t2 = Bc * n * n;
   if (t2 > 0) FN_COUNT(1), k_feat2<<<nblk(t2, 256), 256, 0, s>>>(x, Bc, n, Q, E0);
 }
