@@ -725,6 +725,7 @@ __global__ void k_pair_bwd_reduce(const float* __restrict__ part, int nblocks, i
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ps) return;
   double s = 0.0;
+#pragma unroll 8  // loads ahead of the (unchanged) summation order
   for (int b = 0; b < nblocks; ++b) s += (double)part[(long)b * ps + j];
   if (j < nw) grad_W[j] += s;
   else grad_c[j - nw] += s;
