@@ -594,7 +594,9 @@ __global__ void __launch_bounds__(256) k_pair_bwd(PairBwdArgs a) {
 template <int DIN, int DO>
 __global__ void __launch_bounds__(256) k_pair_bwd_mma(PairBwdArgs a) {
   static_assert(DIN == 32 && DO == 32, "warp-MMA pair backward: 32 -> 32 layers");
-  constexpr int P = kBwdPairs, ZS = DO + 1, ES = DIN + 4;
+  // Zbar rows padded to 36 floats: the dW fragments read Zbar down the pairs,
+  // lane (g, q) at row 2q, column g, which lands on bank 8q + g
+  constexpr int P = kBwdPairs, ZS = DO + 4, ES = DIN + 4;
   static_assert(P % 16 == 0, "whole 16-pair steps");
   __shared__ float Zt[P * ZS];
   __shared__ float Ot[P * ZS];
