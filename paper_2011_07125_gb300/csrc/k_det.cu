@@ -28,14 +28,13 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
                               bool count) {
   T ra[NM], rb[NM];
   const long NSS = a.nss;
-  // determinant only (isotropic envelope, no stored inverse or envelope): the
-  // envelope from FP32 exponentials in both precisions (the FP64 redo of an
-  // ill-conditioned pair repeats the elimination, not the FP32 inputs), and in
-  // FP32 the half-warp LU; the stored forward of the adjoint keeps the
-  // accurate path
-  const bool fast_env = !a.minv && !a.env && !a.full_env;
+  // isotropic envelope: from FP32 exponentials in both precisions (the FP64
+  // redo of an ill-conditioned pair repeats the elimination, not the FP32
+  // inputs), stored for the adjoint when asked; determinant only (no stored
+  // inverse or envelope) in FP32: the half-warp LU
+  const bool fast_env = !a.full_env;
   bool fast = false;
-  if constexpr (std::is_same<T, float>::value) fast = fast_env;
+  if constexpr (std::is_same<T, float>::value) fast = fast_env && !a.minv && !a.env;
 #pragma unroll
   for (int c = 0; c < NM; ++c) {
     ra[c] = (c == sl) ? T(1) : T(0);
@@ -61,6 +60,11 @@ __device__ bool det_pair_body(const DetArgs& a, long mat, const MatId& m, int sl
 #pragma unroll
     for (int c = 0; c < NM; ++c)
       if (c < m.ns) ra[c] = (T)ob[c * ostride] * (T)ev[c];
+    if (a.env) {
+#pragma unroll
+      for (int c = 0; c < NM; ++c)
+        if (c < m.ns) a.env[mat * NSS + sl * m.ns + c] = ev[c];
+    }
   } else if (sl < m.ns) {
     const float* pi = a.pi[m.s] + ((long)m.k * m.ns + sl) * a.N;
     const float* sg = a.sigma[m.s] + ((long)m.k * m.ns + sl) * a.N;
