@@ -187,21 +187,31 @@ def run_reference(args, wl):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def code_only(src: bytes) -> bytes:
+    """C++ source without its comments, whitespace runs collapsed: two sources
+    that differ only in comments or layout compile to the same kernels (none of
+    the hashed sources holds a comment marker inside a string literal)."""
+    import re
+    src = re.sub(rb"/\*.*?\*/", b" ", src, flags=re.S)
+    src = re.sub(rb"//[^\n]*", b" ", src)
+    return b" ".join(src.split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of what the timed GEMM class's traffic depends on: the tensor-core
-    GEMM sources and the network pass (forward() in ferminet.cu) that sizes
-    and tiles its launches."""
+    """Hash of what the timed GEMM class's traffic depends on: the code (not the
+    comments) of the tensor-core GEMM sources and of the network pass
+    (forward() in ferminet.cu) that sizes and tiles its launches."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2011_07125_gb300", "csrc")
     for f in ("k_tc_gemm.cu", "tc_gemm.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+            h.update(code_only(fh.read()))
     with open(os.path.join(csrc, "ferminet.cu"), "rb") as fh:
         src = fh.read()
     start = src.find(b"\nvoid forward(fn_ctx* c")
     end = src.find(b"\n}\n", start)
-    h.update(src[start:end] if start >= 0 and end > start else src)
+    h.update(code_only(src[start:end] if start >= 0 and end > start else src))
     return h.hexdigest()[:16]
 
 

@@ -15,13 +15,14 @@
 // operand is split into hi + lo BF16 parts and the tile accumulates
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 significant bits per operand).
 //
-// Structure: persistent CTAs (one per SM, 320 threads): warp 0 issues TMA loads
-// into a 4-stage shared-memory ring, warp 1 (one elected lane) issues
-// tcgen05.mma into one of two TMEM accumulators (2 x 256 columns) and commits to
-// mbarriers, warps 2-9 run the epilogue (tcgen05.ld; two warps per TMEM lane
-// quarter, splitting the tile's columns) while the next tile accumulates.  Every wait is bounded: after about a
-// second the waiting role sets an abort flag and the status word, all roles
-// drain, and TMEM is released.
+// Structure: persistent CTAs (one per SM, 576 threads): warp 0 issues TMA loads
+// into a shared-memory ring (up to 4 stages, fewer when the residual region
+// takes the space), warp 1 (one lane) issues tcgen05.mma into one of two TMEM
+// accumulators (2 x 256 columns) and commits to mbarriers, warps 2-17 run the
+// epilogue (tcgen05.ld; four warps per TMEM lane quarter, splitting the tile's
+// columns or groups) while the next tile accumulates.  Every wait is bounded:
+// after about two seconds the waiting role sets an abort flag and the status
+// word, all roles drain, and TMEM is released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>

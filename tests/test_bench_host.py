@@ -1,5 +1,6 @@
 """Host-side logic of bench.py (no GPU): the algorithmic byte count used for
-the HBM view of the GEMM-class roofline."""
+the HBM view of the GEMM-class roofline, the key of the DRAM traffic record and
+the launcher of several ranks."""
 import os
 import sys
 
@@ -36,6 +37,17 @@ def test_gemm_class_bytes_match_launch_count(name):
 def test_gemm_class_bytes_c4h6_value():
     # 30 electrons, 92 real columns, 10 nuclei, d1 = 256, d2 = 32, 16 determinants
     assert bench.gemm_class_alg_bytes(synth.workload("c4h6").net) == 29257472
+
+
+def test_source_key_ignores_comments_not_code():
+    """The traffic record's source key: comment and layout edits keep it, a
+    changed token does not."""
+    src = b"int f(int x) {  // doubled\n  return 2 * x; /* no overflow\n check */\n}\n"
+    same = b"int f(int x) {\n\n    return 2 * x;\n}"
+    other = b"int f(int x) { return 3 * x; }"
+    assert bench.code_only(src) == bench.code_only(same) == b"int f(int x) { return 2 * x; }"
+    assert bench.code_only(src) != bench.code_only(other)
+    assert len(bench.kernel_source_hash()) == 16
 
 
 def _bench(*args, env=None):
