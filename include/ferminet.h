@@ -320,9 +320,13 @@ fn_status ferminet_get_tuning(const fn_ctx* ctx, fn_tuning* out);
 fn_status ferminet_set_tuning(fn_ctx* ctx, const fn_tuning* t);
 
 /* Autotuner: times the local-energy pass on d_x [B][n][3] (repeats times per
- * candidate, minimum kept) for every candidate combination of the three
- * fields, installs the fastest in the context and returns it in *best (may be
- * NULL).  Synchronises the stream.  Only meaningful in FN_PREC_MIXED. */
+ * candidate, minimum kept) for every candidate combination of layer_groups,
+ * feature_tile, tangent_chunk and residual_smem, installs the fastest in the
+ * context and returns it in *best (may be NULL).  Synchronises the stream.
+ * Only meaningful in FN_PREC_MIXED.  The built-in defaults (all fields 0) read
+ * the layer residual from global memory; on GB300 the autotuner picks
+ * residual_smem = 1 for every workload measured, where the tensor-core GEMMs
+ * of the local-energy pass take about a third less time. */
 fn_status ferminet_autotune(fn_ctx* ctx, const float* d_x, long B, int repeats, fn_tuning* best);
 
 /* Synchronises the context stream and reads the device status word:
