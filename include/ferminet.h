@@ -325,8 +325,8 @@ fn_status ferminet_set_tuning(fn_ctx* ctx, const fn_tuning* t);
  * context and returns it in *best (may be NULL).  Synchronises the stream.
  * Only meaningful in FN_PREC_MIXED.  The built-in defaults (all fields 0) read
  * the layer residual from global memory; on GB300 the autotuner picks
- * residual_smem = 1 for every workload measured, where the tensor-core GEMMs
- * of the local-energy pass take about a third less time. */
+ * residual_smem = 1 for the C4H6 and eight-geometry C4H4 workloads, whose
+ * tensor-core GEMMs then take about a third less time. */
 fn_status ferminet_autotune(fn_ctx* ctx, const float* d_x, long B, int repeats, fn_tuning* best);
 
 /* Synchronises the context stream and reads the device status word:
