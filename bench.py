@@ -218,15 +218,36 @@ def kernel_source_hash() -> str:
 TRAFFIC_TUNING = ("layer_groups", "residual_smem")  # tuning fields a traffic record is keyed by
 
 
-def recorded_traffic(workload: str, prec: str, tuning=None):
+def layer_groups_used(groups: int, C: int) -> int:
+    """(walker, electron) groups per tile of the layer GEMM for the tuning
+    field layer_groups and C tangent columns per group: the field when it
+    gives a valid tile, else the library's default (the most groups whose tile
+    is at most 256 rows and a multiple of 16)."""
+    if groups > 0 and groups * C <= 256 and (groups * C) % 16 == 0:
+        return groups
+    for g in range(256 // C, 0, -1):
+        if (g * C) % 16 == 0:
+            return g
+    return 0
+
+
+def recorded_traffic(workload: str, prec: str, tuning=None, net=None):
     """DRAM bytes per walker of the timed GEMM class from the committed ncu
     summary (profiles/roofline_traffic.md), or None if the kernel sources have
     changed since the capture or the record's tuning (layer_groups,
-    residual_smem) differs from the timed one."""
+    residual_smem) differs from the timed one.  With the network shape given,
+    layer_groups compares as the tile it selects (0 and the default's group
+    count are the same tile)."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     if not os.path.exists(path):
         return None
     src = kernel_source_hash()
+    C = None if net is None else ((3 * net.n_elec + 2 + 7) // 8) * 8
+
+    def field(t, k):
+        v = int(t.get(k, 0))
+        return layer_groups_used(v, C) if (k == "layer_groups" and C) else v
+
     for line in open(path):
         if not line.startswith("traffic:"):
             continue
@@ -236,7 +257,7 @@ def recorded_traffic(workload: str, prec: str, tuning=None):
         if "tuning" in kv:
             rec = dict(t.split(":", 1) for t in kv["tuning"].split(",") if ":" in t)
             cur = tuning or {}
-            if any(int(rec.get(k, 0)) != int(cur.get(k, 0)) for k in TRAFFIC_TUNING):
+            if any(field(rec, k) != field(cur, k) for k in TRAFFIC_TUNING):
                 continue
         return float(kv["bytes_per_walker"])
     return None
@@ -276,7 +297,7 @@ def tangent_roofline(fn, prec, clocks, pk, pk_kind, workload=None, walkers_per_l
     else:
         peak = _num(pk, "bf16_tflops_sustained", "bf16_tflops") or 1700.0
         bound, note = "tensor", f"bf16 sustained, {pk_kind}"
-    bpw = recorded_traffic(workload, prec, tuning) if workload else None
+    bpw = recorded_traffic(workload, prec, tuning, net) if workload else None
     traffic = bpw * walkers_per_launch if (bpw is not None and walkers_per_launch) else None
     hbm = None
     if net is not None and walkers_per_launch:

@@ -154,13 +154,11 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
   // coordinates in batches of CB: thread (cl, j) forms column j of X_c
   const int cl = tid / NM, j = tid % NM;
   for (int b = 0; b < nb; ++b) {
-    if (b + 1 < nb) {
-      stage(b + 1);
-      asm volatile("cp.async.wait_group 1;\n" ::);
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::);
-    }
-    __syncthreads();  // batch b's tangents are visible to every thread
+    asm volatile("cp.async.wait_group 0;\n" ::);  // batch b, the only copy group in flight
+    // batch b's tangents are visible to every thread, and every thread is done
+    // with batch b - 1: its raw buffer and the X_c tiles may be refilled
+    __syncthreads();
+    if (b + 1 < nb) stage(b + 1);  // lands while batch b is reduced
     const int c = b * CB + cl;
     const bool act = c < n3;
     T x[NM];
@@ -200,7 +198,6 @@ __device__ bool det_tangent_body(const DetArgs& a, long mat, const MatId& m, con
       a.dgrad[mat * n3 + c] = (float)tr;
       part -= (double)tr2;
     }
-    __syncthreads();  // Draw[b & 1] and Xs are refilled next
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(FULL, part, off);

@@ -51,8 +51,13 @@ constexpr int out_stride() { return Q * DO + 4; }
 template <int Q>
 constexpr int task_rows() { return Q == 1 ? 4 : Q; }
 // Resident blocks per SM the kernel is built for (registers and shared memory).
+// LARGE: a layer of the local-energy pass whose one-group tile needs the
+// shared-memory share of two blocks (many electrons).
+template <int Q, bool LAYER, bool MMA = false, bool LARGE = false>
+constexpr int min_blocks() { return (MMA || LARGE) ? 2 : (LAYER ? 3 : 4); }
+// Features per layer task (see k_pair_layer).
 template <int Q, bool LAYER, bool MMA = false>
-constexpr int min_blocks() { return MMA ? 2 : (LAYER ? (Q == 1 ? 3 : 2) : 4); }
+constexpr int task_features() { return (LAYER && Q > 1 && !MMA) ? 4 : 8; }
 
 // D += A B for one m16n8k16 BF16 tile (A row-major 16 x 16, B column-major
 // 16 x 8), FP32 accumulation.
@@ -173,14 +178,19 @@ __device__ __forceinline__ void spin_sums(const PairArgs& a, int tge, const floa
   }
 }
 
-template <int DIN, int DO, int Q, bool LAYER, bool MMA>
-__global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_pair_layer(PairArgs a) {
+template <int DIN, int DO, int Q, bool LAYER, bool MMA, bool LARGE>
+__global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA, LARGE>()) k_pair_layer(PairArgs a) {
   static_assert(DIN % 4 == 0 && (DO % 8 == 0 || !LAYER), "feature counts");
   static_assert(!MMA || (LAYER && DIN == 32 && DO == 32), "warp-MMA contraction: 32 -> 32 layers");
   constexpr int IPS = in_stride<DIN, Q>();
   constexpr int OPS = LAYER ? out_stride<DO, Q>() : IPS;
   constexpr int ORS = LAYER ? DO : DIN;  // row stride of one quantity in the output tile
-  constexpr int FG = LAYER ? DO / 8 : 1;
+  // features per layer task: 8, or 4 in the local-energy pass (Q = 5), whose
+  // five accumulated quantities per feature would otherwise hold the kernel
+  // to two blocks per SM
+  constexpr int FW = task_features<Q, LAYER, MMA>();
+  constexpr int FG = LAYER ? DO / FW : 1;
+  static_assert(!MMA || FW == 8, "warp-MMA tasks cover 8 features");
   constexpr int R = task_rows<Q>();
   extern __shared__ __align__(16) float smem[];
   const int n = a.n, tg = a.tg, tid = threadIdx.x;
@@ -327,7 +337,7 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_p
         }
       }
     } else {
-    // ---- the layer: R rows x 8 features per task ----
+    // ---- the layer: R rows x FW features per task ----
     const int nq = Q == 1 ? (np + 3) / 4 : np;  // tasks per feature group
     for (int task = tid; task < nq * FG; task += kPairThreads) {
       const int pq = task / FG, fg = task - pq * FG;
@@ -336,11 +346,11 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_p
       for (int r = 0; r < R; ++r)
         prow[r] = Q == 1 ? min(pq + r * nq, np - 1) * IPS : pq * IPS + r * DIN;
       // accumulators as feature pairs (2j, 2j + 1): packed FMAs
-      f2_t acc2[R][4];
+      f2_t acc2[R][FW / 2];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc2[r][j] = 0ull;
+        for (int j = 0; j < FW / 2; ++j) acc2[r][j] = 0ull;
 #pragma unroll
       for (int k = 0; k < DIN; k += 4) {
         float4 xv[R];
@@ -348,23 +358,26 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_p
         for (int r = 0; r < R; ++r) xv[r] = *reinterpret_cast<const float4*>(sin + prow[r] + k);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const ulonglong2 w0 = *reinterpret_cast<const ulonglong2*>(sW + (k + kk) * DO + fg * 8);
-          const ulonglong2 w1 = *reinterpret_cast<const ulonglong2*>(sW + (k + kk) * DO + fg * 8 + 4);
+          ulonglong2 w[FW / 4];
+#pragma unroll
+          for (int h = 0; h < FW / 4; ++h)
+            w[h] = *reinterpret_cast<const ulonglong2*>(sW + (k + kk) * DO + fg * FW + 4 * h);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const f2_t xr = f2_splat(comp(xv[r], kk));
-            f2_fma(acc2[r][0], w0.x, xr);
-            f2_fma(acc2[r][1], w0.y, xr);
-            f2_fma(acc2[r][2], w1.x, xr);
-            f2_fma(acc2[r][3], w1.y, xr);
+#pragma unroll
+            for (int h = 0; h < FW / 4; ++h) {
+              f2_fma(acc2[r][2 * h], w[h].x, xr);
+              f2_fma(acc2[r][2 * h + 1], w[h].y, xr);
+            }
           }
         }
       }
-      float acc[R][8];
+      float acc[R][FW];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < FW / 2; ++j) {
           acc[r][2 * j] = f2_lo(acc2[r][j]);
           acc[r][2 * j + 1] = f2_hi(acc2[r][j]);
         }
@@ -375,10 +388,10 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_p
         const int p = Q == 1 ? pq + u * nq : pq;
         if (p >= np) break;
         const float* ip = sin + p * IPS;
-        float ov[Q][8], yv[8];
+        float ov[Q][FW], yv[FW];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int f = fg * 8 + j;
+        for (int j = 0; j < FW; ++j) {
+          const int f = fg * FW + j;
           const float z0 = Q == 1 ? acc[u][j] : acc[0][j];
           const float y = tanhf(z0 + sb[f]);
           const float s = 1.f - y * y;
@@ -394,21 +407,18 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_p
         const long gp = g0 * n + p;  // global pair index
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const float4 o0 = make_float4(ov[q][0], ov[q][1], ov[q][2], ov[q][3]);
-          const float4 o1 = make_float4(ov[q][4], ov[q][5], ov[q][6], ov[q][7]);
-          float* so = sout_l + p * OPS + q * DO + fg * 8;
-          *reinterpret_cast<float4*>(so) = o0;
-          *reinterpret_cast<float4*>(so + 4) = o1;
-          if (a.Eout) {
-            float* go = a.Eout + (gp * Q + q) * DO + fg * 8;
-            *reinterpret_cast<float4*>(go) = o0;
-            *reinterpret_cast<float4*>(go + 4) = o1;
+#pragma unroll
+          for (int h = 0; h < FW / 4; ++h) {
+            const float4 o = make_float4(ov[q][4 * h], ov[q][4 * h + 1], ov[q][4 * h + 2], ov[q][4 * h + 3]);
+            *reinterpret_cast<float4*>(sout_l + p * OPS + q * DO + fg * FW + 4 * h) = o;
+            if (a.Eout) *reinterpret_cast<float4*>(a.Eout + (gp * Q + q) * DO + fg * FW + 4 * h) = o;
           }
         }
         if (a.Y2) {
-          float* gy = a.Y2 + gp * DO + fg * 8;
-          *reinterpret_cast<float4*>(gy) = make_float4(yv[0], yv[1], yv[2], yv[3]);
-          *reinterpret_cast<float4*>(gy + 4) = make_float4(yv[4], yv[5], yv[6], yv[7]);
+#pragma unroll
+          for (int h = 0; h < FW / 4; ++h)
+            *reinterpret_cast<float4*>(a.Y2 + gp * DO + fg * FW + 4 * h) =
+                make_float4(yv[4 * h], yv[4 * h + 1], yv[4 * h + 2], yv[4 * h + 3]);
         }
       }
     }
@@ -422,16 +432,17 @@ __global__ void __launch_bounds__(kPairThreads, min_blocks<Q, LAYER, MMA>()) k_p
   cp_async_wait_all();  // no copy outlives the block
 }
 
-template <int DIN, int DO, int Q, bool LAYER, bool MMA = false>
+template <int DIN, int DO, int Q, bool LAYER, bool MMA = false, bool LARGE = false>
 void launch_inst(cudaStream_t s, PairArgs a) {
-  auto kern = k_pair_layer<DIN, DO, Q, LAYER, MMA>;
-  constexpr int MB = min_blocks<Q, LAYER, MMA>();
+  auto kern = k_pair_layer<DIN, DO, Q, LAYER, MMA, LARGE>;
+  constexpr int MB = min_blocks<Q, LAYER, MMA, LARGE>();
   const size_t budget = kSmemPerSM / MB - 1024;
   static PerDeviceOnce attr;  // the attribute is per function and device
   attr([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget); });
   // groups per tile: about one task (layer) or two output steps (means) per
   // thread, within the shared-memory share of the resident blocks
-  const int per_group = LAYER ? (a.n * (DO / 8) + (Q == 1 ? 3 : 0)) / (Q == 1 ? 4 : 1) : a.C * (int)(a.ldm / 8);
+  constexpr int FW = task_features<Q, LAYER, MMA>();
+  const int per_group = LAYER ? (a.n * (DO / FW) + (Q == 1 ? 3 : 0)) / (Q == 1 ? 4 : 1) : a.C * (int)(a.ldm / 8);
   const int target = LAYER ? kPairThreads : 2 * kPairThreads;
   int tg = (target + per_group - 1) / per_group;
   if (tg < 1) tg = 1;
@@ -448,6 +459,19 @@ void launch_inst(cudaStream_t s, PairArgs a) {
   FN_COUNT(1), kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(a);
 }
 
+// A layer launch: in the local-energy pass, the two-block instance when one
+// group of pair rows does not fit the shared-memory share of three blocks.
+template <int DIN, int DO, int Q>
+void launch_layer(cudaStream_t s, const PairArgs& a) {
+  if constexpr (Q > 1) {
+    if (pair_smem_bytes<DIN, DO, Q, true>(a.n, 1) > kSmemPerSM / min_blocks<Q, true>() - 1024) {
+      launch_inst<DIN, DO, Q, true, false, true>(s, a);
+      return;
+    }
+  }
+  launch_inst<DIN, DO, Q, true>(s, a);
+}
+
 template <int Q>
 bool dispatch(cudaStream_t s, const PairArgs& a, int din, int dout) {
   if (!a.W) {
@@ -459,16 +483,16 @@ bool dispatch(cudaStream_t s, const PairArgs& a, int din, int dout) {
       default: return false;
     }
   }
-  if (din == 4 && dout == 8) return launch_inst<4, 8, Q, true>(s, a), true;
-  if (din == 8 && dout == 8) return launch_inst<8, 8, Q, true>(s, a), true;
-  if (din == 4 && dout == 16) return launch_inst<4, 16, Q, true>(s, a), true;
-  if (din == 16 && dout == 16) return launch_inst<16, 16, Q, true>(s, a), true;
-  if (din == 4 && dout == 32) return launch_inst<4, 32, Q, true>(s, a), true;
+  if (din == 4 && dout == 8) return launch_layer<4, 8, Q>(s, a), true;
+  if (din == 8 && dout == 8) return launch_layer<8, 8, Q>(s, a), true;
+  if (din == 4 && dout == 16) return launch_layer<4, 16, Q>(s, a), true;
+  if (din == 16 && dout == 16) return launch_layer<16, 16, Q>(s, a), true;
+  if (din == 4 && dout == 32) return launch_layer<4, 32, Q>(s, a), true;
   if (din == 32 && dout == 32) {
     // value rows only: in the local-energy pass (Q = 5) the contraction is a
     // small share of the layer, which keeps its FP32 FMAs
     if (Q == 1 && a.mma) return launch_inst<32, 32, 1, true, true>(s, a), true;
-    return launch_inst<32, 32, Q, true>(s, a), true;
+    return launch_layer<32, 32, Q>(s, a), true;
   }
   return false;
 }
@@ -779,7 +803,7 @@ bool pair_layer_supported(int n, int din, int dout, bool layer, int Q, int C, lo
   if (!(din_ok && dout_ok && (Q == 1 || Q == kQ) && ldm % 8 == 0 && ldm >= 2 * d && C >= 1)) return false;
   if (Q == kQ && C < 3 * n + 2) return false;
   // one group per tile must fit in the shared-memory share of a block
-  const int mb = layer ? (Q == 1 ? 3 : 2) : 4;
+  const int mb = layer ? (Q == 1 ? min_blocks<1, true>() : min_blocks<kQ, true, false, true>()) : min_blocks<1, false>();
   const size_t in = (size_t)(layer ? 1 : 2) * n * (Q * din + 4), out = layer ? (size_t)n * (Q * dout + 4) : 0;
   const size_t w = layer ? (size_t)din * dout + dout : 0;
   return sizeof(float) * (in + out + w + 2 * Q * d) <= (size_t)(kSmemPerSM / mb - 1024);

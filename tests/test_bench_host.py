@@ -50,6 +50,14 @@ def test_source_key_ignores_comments_not_code():
     assert len(bench.kernel_source_hash()) == 16
 
 
+def test_layer_groups_compare_as_tiles():
+    """The traffic record's layer_groups matches the tile the library selects:
+    0 is the default tile (as many groups as fit 256 rows in multiples of 16)."""
+    assert bench.layer_groups_used(0, 88) == bench.layer_groups_used(2, 88) == 2   # C4H4: 176-row tiles
+    assert bench.layer_groups_used(0, 96) == 2 and bench.layer_groups_used(1, 96) == 1  # C4H6
+    assert bench.layer_groups_used(0, 16) == 16 and bench.layer_groups_used(3, 16) == 3
+
+
 def _bench(*args, env=None):
     import subprocess
     e = dict(os.environ)

@@ -376,6 +376,34 @@ def test_two_electron_width_outside_fused_kernel():
     assert np.all(de <= bound), (de / bound).max()
 
 
+def test_pair_fused_large_groups():
+    """56 electrons: one (walker, electron) group of the local-energy pass's
+    32 -> 32 two-electron layer needs the shared-memory share of two blocks, so
+    the fused kernel runs its two-block instance; it matches the separate
+    kernels like the three-block instance does on smaller systems."""
+    from paper_2011_07125_gb300.binding import FermiNet
+    net = synth.Net(3, 32, 32, 1, 28, 28, 1)
+    geoms = [synth.atom(56)]
+    wl = synth.Workload("z56", net, geoms, [3], 1.0, 1, 0.02, "fp32", True)
+    P = synth.init_params(oracle.layout(net), seed=3)
+    x = synth.init_walkers(wl, seed=4)
+    fn = FermiNet(net, geoms, counts=[3], precision="fp32")
+    fn.set_params(cuda(P))
+    xx = cuda(x)
+    seeds = torch.linspace(-1.0, 1.0, 3, device="cuda")
+    res = []
+    for unfused in (0, 1):
+        fn.set_tuning(pair_unfused=unfused)
+        out = fn.local_energy(xx)
+        g = fn.logpsi_vjp(xx, seeds)
+        assert fn.sync() == "FN_OK"
+        res.append((out["logpsi"], out["eloc"], g))
+    (l0, e0, g0), (l1, e1, g1) = res
+    torch.testing.assert_close(l0, l1, rtol=1e-6, atol=1e-6)
+    torch.testing.assert_close(e0, e1, rtol=1e-4, atol=1e-4)
+    assert float((g0 - g1).norm() / g1.norm()) < 1e-5
+
+
 @pytest.mark.parametrize("env", [{"FERMINET_PIVOT_TAU": "0.999"}, {"FERMINET_DET64": "1"}])
 def test_fp64_determinant_redo(monkeypatch, env):
     """Every orbital matrix goes through the FP64 redo (flagged by the pivot
