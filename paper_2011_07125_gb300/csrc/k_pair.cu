@@ -11,8 +11,8 @@
 //
 // One pass does both.  A block stages the pair rows of whole (walker,
 // electron i) groups in shared memory (cp.async), applies the layer with 8
-// output features x Q quantities per thread (weights transposed in shared
-// memory), writes the new rows where a later kernel reads them, then expands
+// output features (4 when Q = 5) x Q quantities per thread (weights
+// transposed in shared memory), writes the new rows where a later kernel reads them, then expands
 // the per-spin sums of the new rows into the dense mean rows (FP32, or BF16
 // hi + lo for the tensor-core GEMM).  Without weights the block only forms the
 // means of its input (the input features h^0_ij).
