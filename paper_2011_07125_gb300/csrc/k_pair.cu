@@ -50,11 +50,12 @@ constexpr int out_stride() { return Q * DO + 4; }
 // Rows per thread task: the Q quantities of one pair, or (value pass) four pairs.
 template <int Q>
 constexpr int task_rows() { return Q == 1 ? 4 : Q; }
-// Resident blocks per SM the kernel is built for (registers and shared memory).
-// LARGE: a layer of the local-energy pass whose one-group tile needs the
-// shared-memory share of two blocks (many electrons).
+// Resident blocks per SM the kernel is built for (registers and shared memory):
+// three for every layer instance, the warp-MMA one included; LARGE: a layer of
+// the local-energy pass whose one-group tile needs the shared-memory share of
+// two blocks (many electrons).
 template <int Q, bool LAYER, bool MMA = false, bool LARGE = false>
-constexpr int min_blocks() { return (MMA || LARGE) ? 2 : (LAYER ? 3 : 4); }
+constexpr int min_blocks() { return LARGE ? 2 : (LAYER ? 3 : 4); }
 // Features per layer task (see k_pair_layer).
 template <int Q, bool LAYER, bool MMA = false>
 constexpr int task_features() { return (LAYER && Q > 1 && !MMA) ? 4 : 8; }
